@@ -1,0 +1,355 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the equivalent-operator Grover iterator on GB300.
+
+One step = one Grover search on a synthetic instance: init_uniform, k fused
+iteration passes, then the measurement (success probability, norm, top-M).
+The metric is amplitude-updates/s = N * k per step / time (one update = one
+amplitude through one full iteration).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+  python bench.py --impl reference ...   # the FP64 CPU oracle as reference arm
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs an independent
+replica of the workload on its own GPU (the path is not sharded: no
+collectives on the data path); value = amplitude updates of all ranks / the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+# name -> (n, dtype, M, k or None for the optimal count, seed)
+WORKLOADS = {
+    "n33-c64-m1-k100": (33, "c64", 1, 100, 3300),
+    "n28-c64-m1": (28, "c64", 1, None, 2801),
+    "n28-c64-m4": (28, "c64", 4, None, 2804),
+    "n28-c64-m16": (28, "c64", 16, None, 2816),
+    "n28-c128-m1": (28, "c128", 1, None, 2811),
+    "n28-c128-m16": (28, "c128", 16, None, 2826),
+    "n26-c64-m8-k3000": (26, "c64", 8, 3000, 2608),
+    "n24-c64-m1-k200": (24, "c64", 1, 200, 2401),
+    "n26-c64-m1-k20": (26, "c64", 1, 20, 2621),
+    "n26-c128-m1-k10": (26, "c128", 1, 10, 2631),
+}
+DEFAULT_WORKLOAD = "n33-c64-m1-k100"
+METRIC = "amplitude-updates/s"
+UNIT = "amp-updates/s"
+BYTES_PER_AMP = {"c64": 8, "c128": 16}
+
+
+def workload(name):
+    n, dtype, m, k, seed = WORKLOADS[name]
+    if k is None:
+        import math
+        k = int(math.floor(0.78539816339744830962 * math.sqrt((1 << n) / m)))
+    return dict(name=name, n=n, dtype=dtype, M=m, k=k, seed=seed)
+
+
+def describe(w):
+    return (f"n={w['n']} {'complex64' if w['dtype'] == 'c64' else 'complex128'}, M={w['M']} seeded marked "
+            f"indices, uniform init, {w['k']} iterations + init + measure per step")
+
+
+def config_of(w, n_gpus):
+    state_bytes = (1 << w["n"]) * BYTES_PER_AMP[w["dtype"]]
+    return {"workload": describe(w), "name": w["name"], "n": w["n"], "state_dtype": w["dtype"], "M": w["M"],
+            "k": w["k"], "seed": w["seed"], "state_bytes": state_bytes,
+            "l2": f"inputs larger than L2 ({state_bytes / 2**30:.1f} GiB state, 129 MB L2)",
+            "parallelism": f"replicas x{n_gpus}"}
+
+
+# ---- distributed plumbing (host-side barrier and max over ranks only) -------------------
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def aggregate(elapsed_s: float, units: float, backend_device="cpu"):
+    """(max elapsed over ranks, sum of units over ranks); identity without a process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return elapsed_s, units
+    t = torch.tensor([elapsed_s], dtype=torch.float64, device=backend_device)
+    u = torch.tensor([units], dtype=torch.float64, device=backend_device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+# ---- clocks -----------------------------------------------------------------------------------------
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={CLOCK_FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200"], stdout=open(self.path, "w"),
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---- roofline inputs ----------------------------------------------------------------------------------
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def kernel_source_hash():
+    p = os.path.join(ROOT, "paper_2005_04635_gb300", "csrc", "k_stream.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def recorded_traffic(w):
+    """DRAM bytes per launch of the iteration pass from a committed ncu summary,
+    scaled to this workload's N; None if no summary matches the current source."""
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None
+    src = kernel_source_hash()
+    for fn in sorted(os.listdir(pdir)):
+        if not fn.endswith(".md"):
+            continue
+        text = open(os.path.join(pdir, fn)).read()
+        mh = re.search(r"k_stream\.cu sha256\[:16\]:\s*`?([0-9a-f]{16})", text)
+        mt = re.search(r"traffic_bytes_per_amp_" + w["dtype"] + r":\s*([0-9.]+)", text)
+        if mh and mt and mh.group(1) == src:
+            return float(mt.group(1)) * (1 << w["n"])
+    return None
+
+
+# ---- CPU baseline: the FP64 oracle, single thread ------------------------------------------------------
+def cpu_baseline(seconds: float = 12.0, n: int = 26, seed: int = 2601):
+    import oracle
+    from paper_2005_04635_gb300 import inputs
+    marked = inputs.marked_indices(n, 1, seed)
+    psi = oracle.init_uniform(n)
+    t0 = time.perf_counter()
+    oracle.grover_operator(psi, n, marked, 1)
+    t1 = time.perf_counter()
+    iters = max(1, int(seconds / max(t1 - t0, 1e-6)) - 1)
+    t2 = time.perf_counter()
+    oracle.grover_operator(psi, n, marked, iters)
+    t3 = time.perf_counter()
+    value = (1 << n) * (iters + 1) / ((t1 - t0) + (t3 - t2))
+    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"n={n} (2^{n} complex128 amplitudes), M=1, uniform init, {iters + 1} iterations of the FP64 "
+                      f"operator oracle (plain C, one thread), {((t1 - t0) + (t3 - t2)):.1f} s"}
+
+
+# ---- our arm -------------------------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    from paper_2005_04635_gb300 import binding, inputs
+    binding.lib()
+    w = workload(args.workload)
+    n, dtype, M, k = w["n"], w["dtype"], w["M"], w["k"]
+    N = 1 << n
+    marked = inputs.marked_indices(n, M, w["seed"])
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    st = binding.State(n, dtype, device=dev, stream=stream)
+    mk = binding.Marked(n, marked)
+
+    ev_it = []
+
+    def step(record=False):
+        st.init_uniform()
+        if record:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+        st.iterate(mk, k)
+        if record:
+            b.record(stream)
+            ev_it.append((a, b))
+        ps, nrm = st.success_prob(mk)
+        idx, p = st.measure_topm(min(M, 16))
+        return ps, nrm, idx
+
+    for _ in range(args.warmup):
+        step()
+    st.sync()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ps, nrm, idx = step(record=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier()
+    elapsed = e0.elapsed_time(e1) / 1e3
+    st.sync()
+    units = float(N) * k * args.steps
+    t_max, units_all = aggregate(elapsed, units, backend_device=dev)
+    value = units_all / t_max
+    iter_ms = sum(a.elapsed_time(b) for a, b in ev_it)
+    pass_s = iter_ms / 1e3 / (args.steps * k)
+
+    # end-to-end through the C ABI: host marked list (pinned) in, host results out
+    pinned = torch.empty(M, dtype=torch.int64, pin_memory=True)
+    pinned.numpy()[:] = marked.astype(np.int64)
+    host_idx = pinned.numpy().view(np.uint64)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_steps = max(1, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        mk2 = binding.Marked(n, host_idx)
+        st.init_uniform()
+        st.iterate(mk2, k)
+        st.success_prob(mk2)
+        st.measure_topm(min(M, 16))
+        mk2.close()
+    torch.cuda.synchronize()
+    e2e_elapsed = time.perf_counter() - t0
+    e2e_t, e2e_units = aggregate(e2e_elapsed, float(N) * k * e2e_steps, backend_device=dev)
+
+    if rank != 0:
+        return None
+    peaks, peak_src = measured_peaks()
+    achieved = BYTES_PER_AMP[dtype] * 2 * N / pass_s / 1e9
+    traffic = recorded_traffic(w)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if dtype == "c64" else "f64",
+        "data": "synthetic (seeded marked indices, uniform initial state)",
+        "config": config_of(w, world),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                     "kernel": "k_pass (fused oracle + inversion about the mean + next-mean partial sums)",
+                     "algorithmic_bytes_per_launch": BYTES_PER_AMP[dtype] * 2 * N,
+                     "avg_launch_ms": pass_s * 1e3, "peak_source": f"{peak_src} hbm_gbs"},
+        "e2e": {"value": e2e_units / e2e_t, "unit": UNIT, "h2d_bytes_per_step": 8 * M,
+                "d2h_bytes_per_step": 16 * min(M, 16) + 16, "steps": e2e_steps},
+        "gpu_launches": args.steps * (k + 5),
+        "clocks": clk,
+        "result_check": {"p_success": ps, "norm": nrm, "top": [int(x) for x in idx]},
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline()
+    return out
+
+
+# ---- reference arm: the oracle on the host cores -----------------------------------------------------
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return None
+    import oracle
+    from paper_2005_04635_gb300 import inputs
+    w = workload(args.workload)
+    n_s, iters = 24, 2  # bounded sample of the workload: 2^24 amplitudes, 2 iterations per step
+    marked = inputs.marked_indices(n_s, min(w["M"], 1 << n_s), w["seed"])
+    psi = oracle.init_uniform(n_s)
+    for _ in range(args.warmup):
+        oracle.grover_operator(psi, n_s, marked, iters)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.grover_operator(psi, n_s, marked, iters)
+    dt = time.perf_counter() - t0
+    value = (1 << n_s) * iters * args.steps / dt
+    sample = (f"each step: n={n_s} (2^{n_s} complex128 amplitudes), M={len(marked)}, {iters} iterations of the "
+              f"FP64 operator oracle (plain C, one thread), standing in for the {w['name']} workload")
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded marked indices, uniform initial state)", "config": config_of(w, world),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    out = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+    try:
+        import torch.distributed as dist
+        if dist.is_available() and dist.is_initialized():
+            dist.destroy_process_group()
+    except Exception:
+        pass
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,198 @@
+/*
+ * grover.h -- C ABI of libgrover.so, a GB300 (sm_103a) Grover search
+ * state-vector simulator built around the equivalent-operator method of
+ * Chattopadhyay & Menon, "Fast simulation of Grover's quantum search on
+ * classical computer" (arXiv 2005.04635).
+ *
+ * The method (section "Proposed Simulation Method"): one Grover iteration
+ * G = (2|psi><psi| - I) O is the oracle phase flip of the solution states
+ * (Algorithm "n-qubit Oracle") followed by the inversion about the mean
+ * (Algorithm "n-qubit Inversion about Mean"), c_x <- 2<c> - c_x with <c> the
+ * complex arithmetic mean of all N = 2^n amplitudes.  The conventional circuit
+ * (section "Background", conventional grover_search) applies H^{(x)n}, the
+ * conditional phase shift 2|0><0| - I and H^{(x)n} instead of the inversion.
+ *
+ * Conventions for every call
+ *   - State layout: N = 2^n interleaved complex amplitudes (re, im) in a
+ *     caller-owned device buffer, complex64 (GROVER_C64, 8 B each) or
+ *     complex128 (GROVER_C128, 16 B each), 16-byte aligned; the index is the
+ *     basis state (section "Quantum State").
+ *   - Streams: every call that launches work runs it on the stream given to
+ *     grover_create (a cudaStream_t passed as void*; NULL = legacy default
+ *     stream) and returns without waiting, unless stated otherwise.  Device-side
+ *     failures (a bounded wait that gave up) are reported by grover_sync and by
+ *     the calls that read results back.
+ *   - Errors: every call returns a grover_status; nothing aborts or throws.
+ *     grover_last_error gives a message for the last failure on a handle.
+ *   - Threads: a handle or marked set must not be used by two host threads at
+ *     once.  Handles on different streams are independent.
+ *   - Sizes: 1 <= n <= 33 for GROVER_C64 and 1 <= n <= 32 for GROVER_C128,
+ *     bounded in practice by device memory (n = 33 complex64 is 64 GiB).
+ *   - There is no CPU fallback: without a usable CUDA device every call that
+ *     needs one returns GROVER_ECUDA.
+ */
+#ifndef GROVER_H
+#define GROVER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GROVER_OK = 0,
+    GROVER_EINVAL = 1,       /* bad argument: NULL pointer, n out of range, misaligned buffer */
+    GROVER_ENOMEM = 2,       /* a host or device allocation failed */
+    GROVER_ECUDA = 3,        /* a CUDA runtime call failed (message in grover_last_error) */
+    GROVER_ETIMEOUT = 4,     /* a bounded device-side wait gave up (state is undefined) */
+    GROVER_EUNSORTED = 5,    /* marked list not in increasing order */
+    GROVER_EDUP = 6,         /* marked list holds an index twice */
+    GROVER_ERANGE = 7,       /* marked index >= N, bitmask of the wrong size or with bits >= N */
+    GROVER_EUNSUPPORTED = 8  /* valid request this build does not provide */
+} grover_status;
+
+typedef enum { GROVER_C64 = 0, GROVER_C128 = 1 } grover_dtype;
+
+/* How the complex mean <c> is accumulated (section "Inversion About Mean
+ * Operator"; the paper sums Re and Im separately in one running sum).  Every
+ * mode combines the per-block partial sums in FP64 in a fixed order, so a
+ * result is bitwise reproducible run to run.
+ *   GROVER_ACC_DEFAULT: GROVER_ACC_FP64.
+ *   GROVER_ACC_FP32:    complex64 only; plain FP32 running sum per thread and an
+ *                       FP32 tree across the block.
+ *   GROVER_ACC_KAHAN:   complex64 only; Neumaier-compensated FP32 running sum
+ *                       per thread and an FP32 tree across the block.
+ *   GROVER_ACC_FP64:    complex64: FP32 sum of each thread's 2..8 amplitudes
+ *                       per load group, FP64 above that; complex128: FP64
+ *                       throughout. */
+typedef enum {
+    GROVER_ACC_DEFAULT = 0,
+    GROVER_ACC_FP32 = 1,
+    GROVER_ACC_KAHAN = 2,
+    GROVER_ACC_FP64 = 3
+} grover_accum;
+
+typedef struct grover_state grover_state;   /* opaque: n, dtype, buffer, stream, scratch, cached mean */
+typedef struct grover_marked grover_marked; /* opaque: validated set of solution states on the device */
+
+/* ---- handles ----------------------------------------------------------- */
+
+/* Binds a state handle to a caller-owned device buffer of N = 2^n amplitudes
+ * (section "Quantum State": psi[N], index = basis state).  dev_amps must be a
+ * device pointer, 16-byte aligned, holding N elements of dtype; it is neither
+ * initialised nor freed by the library.  cuda_stream is a cudaStream_t (or
+ * NULL).  The library allocates a small device scratch area (< 1 MiB) that
+ * grover_destroy frees.  *out is set only on GROVER_OK.  Synchronous. */
+grover_status grover_create(grover_state **out, int n_qubits, grover_dtype dtype,
+                            void *dev_amps, void *cuda_stream);
+
+/* Waits for the handle's stream, then frees its scratch (not the amplitudes).
+ * NULL is accepted. */
+grover_status grover_destroy(grover_state *s);
+
+/* Selects the accumulation of the complex mean (see grover_accum).
+ * GROVER_EINVAL for FP32/KAHAN on a complex128 state. */
+grover_status grover_set_accum(grover_state *s, grover_accum mode);
+
+/* ---- state preparation ------------------------------------------------- */
+
+/* psi = H^{(x)n}|0...0>, written directly as c_i = 1/sqrt(N) rounded to the
+ * storage type (both grover_search algorithms, first two steps). */
+grover_status grover_init_uniform(grover_state *s);
+
+/* Copies N amplitudes of the handle's dtype from amps (host memory if
+ * amps_on_device == 0, device memory otherwise) into the state.  The copy is
+ * not renormalised.  A host source is read before the call returns. */
+grover_status grover_init_state(grover_state *s, const void *amps, int amps_on_device);
+
+/* ---- marked sets (the oracle's data k[] in Algorithm "n-qubit Oracle") -- */
+
+/* Builds a marked set for n-qubit states from a HOST list of m indices, which
+ * must be strictly increasing (GROVER_EUNSORTED if an index is smaller than its
+ * predecessor, GROVER_EDUP if equal) and < 2^n (GROVER_ERANGE).  m = 0 gives the
+ * empty set (O = I).  The list is copied to the device; for m > 256 a bitmask
+ * is built on the device as well.  *out is set only on GROVER_OK.  Synchronous. */
+grover_status grover_marked_from_list(grover_marked **out, int n_qubits,
+                                      const uint64_t *idx, size_t m);
+
+/* Builds a marked set from a bitmask of nwords = ceil(2^n / 32) uint32 words:
+ * index x is marked iff bit (x % 32) of word x / 32 is set.  words is host
+ * memory if on_device == 0, else device memory.  GROVER_ERANGE if nwords is
+ * wrong or a bit >= 2^n is set.  Synchronous (counts the set bits). */
+grover_status grover_marked_from_bitmask(grover_marked **out, int n_qubits,
+                                         const uint32_t *words, size_t nwords,
+                                         int on_device);
+
+/* Number of marked indices M. */
+grover_status grover_marked_count(const grover_marked *mk, uint64_t *m);
+
+/* Frees a marked set (waits for the device first).  NULL is accepted. */
+grover_status grover_marked_destroy(grover_marked *mk);
+
+/* ---- the Grover operators ---------------------------------------------- */
+
+/* Algorithm "n-qubit Oracle": c_x <- -c_x for every marked x.  The marked set
+ * must have been built for the state's n (GROVER_EINVAL otherwise). */
+grover_status grover_oracle(grover_state *s, const grover_marked *mk);
+
+/* Algorithm "n-qubit Inversion about Mean" (section "Inversion About Mean
+ * Operator"): <c> = (1/N) sum_i c_i over ALL amplitudes, then
+ * c_i <- 2<c> - c_i for all i.  Equals applying Delta = 2|psi><psi| - I. */
+grover_status grover_diffuse(grover_state *s);
+
+/* k Grover iterations of the proposed grover_search loop: each applies the
+ * oracle then the inversion about the mean, as one fused device pass over the
+ * state per iteration (the mean used by iteration t+1 is accumulated while
+ * iteration t stores).  k = 0 is a no-op. */
+grover_status grover_iterate(grover_state *s, const grover_marked *mk, uint64_t k);
+
+/* k iterations of the conventional circuit (section "Background",
+ * conventional grover_search): oracle, H^{(x)n}, 2|0><0| - I, H^{(x)n}, with
+ * H^{(x)n} applied as blocked Walsh-Hadamard tiles on the tensor cores.  The
+ * result equals grover_iterate's up to rounding (no global phase).
+ * GROVER_EUNSUPPORTED where this build has no gate path for the dtype / n. */
+grover_status grover_iterate_gate(grover_state *s, const grover_marked *mk, uint64_t k);
+
+/* floor(pi/4 * sqrt(2^n / m)), the iteration count that maximises the success
+ * probability for m marked states out of 2^n (the paper's loop bound
+ * pi*sqrt(N)/4 read as a floor, generalised to m solutions); 0 if m == 0 or
+ * n is out of [1, 63]. */
+uint64_t grover_optimal_iterations(int n_qubits, uint64_t m);
+
+/* ---- measurement (section "Simulation Results", measurement outcome) --- */
+
+/* p_i = |c_i|^2 in FP64 for all N basis states, written to out (N doubles;
+ * host memory if out_on_device == 0, else device).  Synchronous for host
+ * output. */
+grover_status grover_measure_probs(grover_state *s, double *out, int out_on_device);
+
+/* The m most probable basis states (1 <= m <= 16, m <= N) ordered by
+ * (probability desc, index asc), written to HOST arrays idx[m], p[m]
+ * (p in FP64).  Synchronous. */
+grover_status grover_measure_topm(grover_state *s, size_t m, uint64_t *idx, double *p);
+
+/* P_success = sum over marked x of |c_x|^2 and norm = sum over all i of
+ * |c_i|^2, FP64 accumulation, written to HOST doubles (either may be NULL).
+ * Synchronous. */
+grover_status grover_success_prob(grover_state *s, const grover_marked *mk,
+                                  double *p_success, double *norm);
+
+/* ---- synchronisation and errors ----------------------------------------- */
+
+/* Waits for the handle's stream and reads the device status word:
+ * GROVER_ETIMEOUT if a bounded device-side wait gave up since the last call. */
+grover_status grover_sync(grover_state *s);
+
+/* Message for the last failure on s (s may be NULL: last failure on this host
+ * thread).  The string is owned by the library. */
+const char *grover_last_error(const grover_state *s);
+
+/* Name of a status code. */
+const char *grover_status_string(grover_status st);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GROVER_H */

@@ -1,0 +1,209 @@
+"""Thin ctypes binding of libgrover.so (C ABI in include/grover.h).
+
+Argument marshalling only: torch supplies device memory (a complex64 or
+complex128 CUDA tensor of 2^n elements) and the stream; every computation runs
+in the library's CUDA kernels.  There is no fallback: if the library is not
+built, or no CUDA device is usable, calls raise ``GroverError``.
+
+The module-level functions carry the C names; ``State`` and ``Marked`` are
+small owners of the opaque handles.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import library_path
+
+GROVER_OK = 0
+STATUS = {0: "GROVER_OK", 1: "GROVER_EINVAL", 2: "GROVER_ENOMEM", 3: "GROVER_ECUDA", 4: "GROVER_ETIMEOUT",
+          5: "GROVER_EUNSORTED", 6: "GROVER_EDUP", 7: "GROVER_ERANGE", 8: "GROVER_EUNSUPPORTED"}
+C64, C128 = 0, 1
+ACC = {"default": 0, "fp32": 1, "kahan": 2, "fp64": 3}
+
+# every symbol include/grover.h declares, with its ctypes signature
+_vp = ctypes.c_void_p
+_SIGS = {
+    "grover_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, _vp, _vp]),
+    "grover_destroy": (ctypes.c_int, [_vp]),
+    "grover_set_accum": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "grover_init_uniform": (ctypes.c_int, [_vp]),
+    "grover_init_state": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
+    "grover_marked_from_list": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, _vp, ctypes.c_size_t]),
+    "grover_marked_from_bitmask": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, _vp, ctypes.c_size_t, ctypes.c_int]),
+    "grover_marked_count": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64)]),
+    "grover_marked_destroy": (ctypes.c_int, [_vp]),
+    "grover_oracle": (ctypes.c_int, [_vp, _vp]),
+    "grover_diffuse": (ctypes.c_int, [_vp]),
+    "grover_iterate": (ctypes.c_int, [_vp, _vp, ctypes.c_uint64]),
+    "grover_iterate_gate": (ctypes.c_int, [_vp, _vp, ctypes.c_uint64]),
+    "grover_optimal_iterations": (ctypes.c_uint64, [ctypes.c_int, ctypes.c_uint64]),
+    "grover_measure_probs": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
+    "grover_measure_topm": (ctypes.c_int, [_vp, ctypes.c_size_t, _vp, _vp]),
+    "grover_success_prob": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "grover_sync": (ctypes.c_int, [_vp]),
+    "grover_last_error": (ctypes.c_char_p, [_vp]),
+    "grover_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+_lib = None
+
+
+class GroverError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def lib():
+    """Loads libgrover.so (built in-tree by ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise GroverError(3, f"{path} is not built; run __graft_entry__.build()")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(st: int, handle=None):
+    if st != GROVER_OK:
+        msg = lib().grover_last_error(handle)
+        raise GroverError(st, msg.decode() if msg else "")
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def grover_optimal_iterations(n: int, m: int) -> int:
+    return int(lib().grover_optimal_iterations(n, m))
+
+
+class Marked:
+    """A validated marked set (the oracle's solution list) on the device."""
+
+    def __init__(self, n: int, indices=None, bitmask=None):
+        h = _vp()
+        if bitmask is not None:
+            if hasattr(bitmask, "data_ptr"):  # device tensor of int32/uint32 words
+                st = lib().grover_marked_from_bitmask(ctypes.byref(h), n, bitmask.data_ptr(), bitmask.numel(), 1)
+            else:
+                w = np.ascontiguousarray(np.asarray(bitmask, dtype=np.uint32))
+                st = lib().grover_marked_from_bitmask(ctypes.byref(h), n, w.ctypes.data, w.size, 0)
+        else:
+            idx = np.ascontiguousarray(np.asarray([] if indices is None else indices, dtype=np.uint64).reshape(-1))
+            st = lib().grover_marked_from_list(ctypes.byref(h), n, idx.ctypes.data if idx.size else None, idx.size)
+        _check(st)
+        self.n = n
+        self.handle = h
+
+    @property
+    def count(self) -> int:
+        m = ctypes.c_uint64()
+        _check(lib().grover_marked_count(self.handle, ctypes.byref(m)))
+        return int(m.value)
+
+    def close(self):
+        if self.handle:
+            _check(lib().grover_marked_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class State:
+    """A state handle bound to a caller-owned CUDA tensor of 2^n amplitudes."""
+
+    def __init__(self, n: int, dtype: str = "c64", amps=None, stream=None, device=None):
+        import torch
+        tdt = {"c64": torch.complex64, "c128": torch.complex128}[dtype]
+        if amps is None:
+            amps = torch.empty(1 << n, dtype=tdt, device=device or "cuda")
+        if amps.dtype != tdt or amps.numel() != (1 << n) or not amps.is_contiguous() or not amps.is_cuda:
+            raise ValueError("amps must be a contiguous CUDA tensor of 2**n elements of the given dtype")
+        self.n, self.dtype, self.amps = n, dtype, amps
+        self.stream = stream
+        h = _vp()
+        _check(lib().grover_create(ctypes.byref(h), n, C64 if dtype == "c64" else C128, amps.data_ptr(),
+                                   _stream_ptr(stream)))
+        self.handle = h
+
+    # -- calls with the C names -------------------------------------------------------
+    def set_accum(self, mode: str):
+        _check(lib().grover_set_accum(self.handle, ACC[mode]), self.handle)
+
+    def init_uniform(self):
+        _check(lib().grover_init_uniform(self.handle), self.handle)
+
+    def init_state(self, amps):
+        """amps: a CUDA tensor (device copy) or a numpy array (host copy)."""
+        if hasattr(amps, "data_ptr"):
+            _check(lib().grover_init_state(self.handle, amps.data_ptr(), 1 if amps.is_cuda else 0), self.handle)
+        else:
+            npdt = np.complex64 if self.dtype == "c64" else np.complex128
+            a = np.ascontiguousarray(np.asarray(amps, dtype=npdt))
+            if a.size != (1 << self.n):
+                raise ValueError("wrong number of amplitudes")
+            _check(lib().grover_init_state(self.handle, a.ctypes.data, 0), self.handle)
+
+    def oracle(self, marked: Marked):
+        _check(lib().grover_oracle(self.handle, marked.handle), self.handle)
+
+    def diffuse(self):
+        _check(lib().grover_diffuse(self.handle), self.handle)
+
+    def iterate(self, marked: Marked, k: int):
+        _check(lib().grover_iterate(self.handle, marked.handle, int(k)), self.handle)
+
+    def iterate_gate(self, marked: Marked, k: int):
+        _check(lib().grover_iterate_gate(self.handle, marked.handle, int(k)), self.handle)
+
+    def measure_probs(self, out=None):
+        """Returns p_i = |c_i|^2 (FP64): into a CUDA tensor if given, else a numpy array."""
+        if out is not None:
+            _check(lib().grover_measure_probs(self.handle, out.data_ptr(), 1), self.handle)
+            return out
+        p = np.empty(1 << self.n, dtype=np.float64)
+        _check(lib().grover_measure_probs(self.handle, p.ctypes.data, 0), self.handle)
+        return p
+
+    def measure_topm(self, m: int):
+        idx = np.zeros(m, dtype=np.uint64)
+        p = np.zeros(m, dtype=np.float64)
+        _check(lib().grover_measure_topm(self.handle, m, idx.ctypes.data, p.ctypes.data), self.handle)
+        return idx, p
+
+    def success_prob(self, marked: Marked):
+        ps, nrm = ctypes.c_double(), ctypes.c_double()
+        _check(lib().grover_success_prob(self.handle, marked.handle, ctypes.byref(ps), ctypes.byref(nrm)),
+               self.handle)
+        return ps.value, nrm.value
+
+    def sync(self):
+        _check(lib().grover_sync(self.handle), self.handle)
+
+    def close(self):
+        if self.handle:
+            _check(lib().grover_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

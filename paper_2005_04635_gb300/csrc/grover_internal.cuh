@@ -1,0 +1,125 @@
+// grover_internal.cuh -- types shared by the translation units of libgrover.
+//
+// Device-side views, the handle layout and the host-side launchers that the C
+// ABI (grover_api.cu) calls.  Kernels live in k_stream.cu (init, oracle, fused
+// iteration pass, mean reduction) and k_measure.cu (probabilities, norm,
+// top-m).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "grover.h"
+
+namespace grv {
+
+constexpr int kThreads = 256;           // threads per CTA of the streaming kernels
+constexpr int kMaxGrid = 4096;          // upper bound on CTAs of a streaming launch
+constexpr uint64_t kListMax = 256;      // larger marked lists also get a bitmask
+constexpr int kTopMMax = 16;            // grover_measure_topm limit
+constexpr int kTopMGrid = 1024;         // CTAs of a top-m launch
+
+enum MarkMode : int { MARK_NONE = 0, MARK_LIST = 1, MARK_BITS = 2 };
+
+// Device view of a marked set.
+struct MarkedDev {
+    const uint64_t *list;   // sorted unique indices (MARK_LIST), else unused
+    const uint32_t *words;  // bitmask (MARK_BITS), else unused
+    uint64_t m;             // number of marked indices
+    int mode;               // MarkMode used by the streaming kernels
+};
+
+// Candidate of the top-m selection.
+struct Cand {
+    double p;
+    uint64_t idx;
+};
+
+// Device scratch owned by one state handle (one cudaMalloc, carved up).
+struct Scratch {
+    double2 *partials;      // [kMaxGrid] per-CTA partial sums
+    double2 *mu;            // [2] double-buffered complex mean
+    unsigned *ticket;       // [1] last-CTA-done counter (always left at 0)
+    int *status;            // [1] device status word (0 = ok)
+    Cand *cand;             // [(kTopMGrid + 1) * kTopMMax] per-CTA top-m candidates + result
+    double2 *red;           // [4] reduction outputs (norm, success)
+    double *probs_tmp;      // [kProbsChunk] staging for host probability output
+};
+constexpr size_t kProbsChunk = size_t(1) << 22;  // 32 MiB of doubles
+
+// Launch geometry derived once per handle.
+struct Geometry {
+    int sm_count;
+    int dev;
+    long long l2_bytes;
+};
+
+// Everything a streaming kernel launch needs.
+struct PassArgs {
+    void *amps;
+    uint64_t nvec;          // number of 16-byte vectors in the state
+    MarkedDev mk;
+    const double2 *mu_in;   // mean used by this pass (device)
+    double2 *mu_out;        // mean produced for the next pass (device)
+    double2 *partials;
+    unsigned *ticket;
+    double inv_n;           // 1 / N
+    bool stream_hint;       // state larger than L2: streaming cache hints
+};
+
+// ---- launchers (k_stream.cu) ---------------------------------------------
+cudaError_t launch_init_uniform(void *amps, int n, grover_dtype dt, cudaStream_t st,
+                                const Geometry &g);
+// One fused iteration pass: c <- 2*mu_in - flip(c), store, and
+// mu_out = mean(flip(c_new)).
+// Both flips use args.mk (MARK_NONE: no flip).
+cudaError_t launch_pass(const PassArgs &a, grover_dtype dt, grover_accum acc, cudaStream_t st,
+                        const Geometry &g);
+// Mean only: mu_out = mean(flip(c)).
+cudaError_t launch_reduce(const PassArgs &a, grover_dtype dt, grover_accum acc, cudaStream_t st,
+                          const Geometry &g);
+// Oracle alone: c_x <- -c_x for marked x.
+cudaError_t launch_oracle(void *amps, int n, grover_dtype dt, const MarkedDev &mk,
+                          cudaStream_t st, const Geometry &g);
+// Bitmask helpers for marked sets.
+cudaError_t launch_bits_from_list(uint32_t *words, uint64_t nwords, const uint64_t *list,
+                                  uint64_t m, cudaStream_t st);
+cudaError_t launch_bits_check_count(const uint32_t *words, uint64_t nwords, int n,
+                                    unsigned long long *count_out, int *bad_out,
+                                    cudaStream_t st);
+
+// ---- launchers (k_measure.cu) --------------------------------------------
+cudaError_t launch_probs(const void *amps, grover_dtype dt, uint64_t first, uint64_t count,
+                         double *out, cudaStream_t st, const Geometry &g);
+// red[0].x = norm, red[1].x = success probability
+cudaError_t launch_norm_success(const void *amps, int n, grover_dtype dt, const MarkedDev &mk,
+                                Scratch &sc, cudaStream_t st, const Geometry &g);
+cudaError_t launch_topm(const void *amps, int n, grover_dtype dt, int m, Scratch &sc,
+                        cudaStream_t st, const Geometry &g);
+
+}  // namespace grv
+
+// Handle layout (opaque in the C ABI).
+struct grover_state {
+    int n;
+    uint64_t N;
+    grover_dtype dtype;
+    grover_accum acc;
+    void *amps;
+    cudaStream_t stream;
+    grv::Geometry geo;
+    void *scratch_base;
+    grv::Scratch sc;
+    int mu_slot;            // which mu[] holds the current mean
+    bool mu_valid;          // cached mean of flip_key(c) is valid
+    uint64_t mu_key;        // 0: mean of c itself; else id of the marked set applied
+    char err[512];
+};
+
+struct grover_marked {
+    int n;
+    uint64_t id;            // unique per marked set in this process
+    grv::MarkedDev dev;
+    void *list_mem;
+    void *words_mem;
+};

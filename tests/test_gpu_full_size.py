@@ -1,0 +1,84 @@
+"""Full-size runs (the benchmark's launch configuration) against the oracle's
+closed form for a uniform initial state:
+  marked amplitude sin((2k+1)theta)/sqrt(M), unmarked cos((2k+1)theta)/sqrt(N-M).
+
+The whole state is checked on the device (the group invariant: every unmarked
+amplitude equals one value, every marked one another), then the two values are
+compared with the closed form one by one.
+
+complex64 bound: each iteration adds an error vector of norm <= 3 * 2^-24 (one
+FP32 rounding per stored amplitude, norm <= 2^-24, plus the FP32 rounding of
+2 mu shared by all N amplitudes, norm <= sqrt(N) * 2^-24 * 2|mu| <= 2 * 2^-24);
+the iteration is unitary, so after k iterations |error| <= 3k * 2^-24.
+P_success must be within 1e-4 of the FP64 value.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2005_04635_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2005_04635_gb300 import binding
+    binding.lib()
+    return binding
+
+
+def run_and_check(B, n, m, dtype, k, seed):
+    marked = inputs.marked_indices(n, m, seed)
+    mk = B.Marked(n, marked)
+    st = B.State(n, dtype)
+    st.init_uniform()
+    st.iterate(mk, k)
+    ps, nrm = st.success_prob(mk)
+    idx, p = st.measure_topm(m)
+    st.sync()
+    a = st.amps
+    mi = torch.as_tensor(marked.astype(np.int64), device=a.device)
+    mvals = a[mi]
+    # one unmarked index: the smallest index not in the list
+    u = next(x for x in range(m + 1) if x not in set(marked.tolist()))
+    uval = a[u]
+    n_diff_unmarked = int(torch.count_nonzero(a != uval).item())
+    assert bool(torch.all(mvals == mvals[0]).item()), "marked amplitudes differ"
+    assert n_diff_unmarked == m, "an unmarked amplitude differs from the others"
+    am, au = oracle.closed_form_uniform(n, m, k)
+    got_m = complex(mvals[0].item())
+    got_u = complex(uval.item())
+    tol = 1e-11 if dtype == "c128" else 3 * k * 2.0 ** -24
+    assert abs(got_m - am) <= tol and abs(got_u - au) <= tol, (got_m, am, got_u, au)
+    p_ref = m * am * am
+    assert abs(ps - p_ref) <= (1e-11 if dtype == "c128" else 1e-4)
+    if dtype == "c128":
+        assert abs(1.0 - nrm) <= 1e-12
+    assert sorted(idx.tolist()) == marked.tolist()
+    del st
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("m", [1, 4, 16])
+def test_n28_c64_full_optimal(B, m):
+    n = 28
+    run_and_check(B, n, m, "c64", B.grover_optimal_iterations(n, m), seed=2800 + m)
+
+
+@pytest.mark.parametrize("m", [1, 16])
+def test_n28_c128_full_optimal(B, m):
+    n = 28
+    run_and_check(B, n, m, "c128", B.grover_optimal_iterations(n, m), seed=2810 + m)
+
+
+def test_n33_c64_100_iterations(B):
+    free, _ = torch.cuda.mem_get_info()
+    if free < (80 << 30):
+        pytest.skip("needs 80 GB of free device memory")
+    run_and_check(B, 33, 1, "c64", 100, seed=3300)

@@ -1,0 +1,239 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances
+  * complex128: max |gpu - oracle| <= 1e-11 after the full optimal run, and
+    |1 - norm| <= 1e-12; top-m / argmax indices bit-exact.
+  * complex64: the state is rounded to FP32 at every store, so each iteration
+    adds at most one FP32 rounding of a value bounded by max|c| + 2|mu| <= 2
+    (the update) plus the FP32 rounding of 2mu; unitary propagation does not
+    amplify earlier errors.  Bound used: (k + 1) * 2^-22.  P_success within
+    1e-4 of the oracle.
+  * Under a uniform initial state every unmarked amplitude goes through the
+    same operations on the same values, so all unmarked (and all marked)
+    amplitudes must be bitwise equal: an exact check of indexing and tails.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2005_04635_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2005_04635_gb300 import binding
+    binding.lib()
+    return binding
+
+
+def c64_tol(k):
+    return (k + 1) * 2.0 ** -22
+
+
+def to_np(st):
+    torch.cuda.synchronize()
+    return st.amps.cpu().numpy().astype(np.complex128)
+
+
+def check_groups(psi, marked):
+    mask = np.zeros(psi.size, dtype=bool)
+    mask[np.asarray(marked, dtype=np.int64)] = True
+    for grp in (psi[mask], psi[~mask]):
+        if grp.size:
+            assert np.all(grp == grp[0]), "amplitudes of one group differ bitwise"
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("n,m", [(1, 1), (2, 1), (3, 1), (5, 2), (6, 1), (9, 3), (12, 1), (12, 4), (16, 16), (17, 1), (20, 1)])
+def test_uniform_full_run(B, dtype, n, m):
+    marked = inputs.marked_indices(n, m, seed=n * 100 + m)
+    k = B.grover_optimal_iterations(n, m)
+    mk = B.Marked(n, marked)
+    st = B.State(n, dtype)
+    st.init_uniform()
+    st.iterate(mk, k)
+    ps, nrm = st.success_prob(mk)
+    st.sync()
+    got = to_np(st)
+    ref = oracle.grover_operator(oracle.init_uniform(n), n, marked, k)
+    err = np.max(np.abs(got - ref))
+    if dtype == "c128":
+        assert err <= 1e-11
+        assert abs(1.0 - nrm) <= 1e-12
+        assert abs(ps - oracle.success_prob(ref, n, marked)) <= 1e-12
+    else:
+        assert err <= c64_tol(k)
+        assert abs(ps - oracle.success_prob(ref, n, marked)) <= 1e-4
+    check_groups(got, marked)
+    if m <= 16 and m < (1 << n) // 4:
+        idx, p = st.measure_topm(m)
+        assert sorted(idx.tolist()) == marked.tolist()
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("n,m,k", [(4, 3, 7), (10, 8, 60), (14, 8, 200), (15, 5, 31)])
+def test_gaussian_init(B, dtype, n, m, k):
+    marked = inputs.marked_indices(n, m, seed=7 * n)
+    psi0 = inputs.gaussian_state(n, seed=11 * n)
+    if dtype == "c64":
+        psi0 = psi0.astype(np.complex64).astype(np.complex128)  # the oracle starts from the stored values
+    mk = B.Marked(n, marked)
+    st = B.State(n, dtype)
+    st.init_state(psi0)
+    st.iterate(mk, k)
+    st.sync()
+    got = to_np(st)
+    ref = oracle.grover_operator(psi0.copy(), n, marked, k)
+    err = np.max(np.abs(got - ref))
+    assert err <= (1e-11 if dtype == "c128" else c64_tol(k))
+    # top-m on the same final state: bit-exact against the oracle's selection
+    idx, p = st.measure_topm(min(16, 1 << n))
+    oidx, op = oracle.topm(got, n, min(16, 1 << n))
+    assert np.array_equal(idx, oidx) and np.array_equal(p, op)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_large_marked_set_uses_bitmask(B, dtype):
+    n, m = 13, 300  # more than 256 indices: the library adds a bitmask
+    marked = inputs.marked_indices(n, m, seed=5)
+    k = 5
+    psi0 = inputs.gaussian_state(n, seed=6)
+    if dtype == "c64":
+        psi0 = psi0.astype(np.complex64).astype(np.complex128)
+    ref = oracle.grover_operator(psi0.copy(), n, marked, k)
+    for mk in (B.Marked(n, marked), B.Marked(n, bitmask=inputs.bitmask(n, marked))):
+        assert mk.count == m
+        st = B.State(n, dtype)
+        st.init_state(psi0)
+        st.iterate(mk, k)
+        ps, _ = st.success_prob(mk)
+        got = to_np(st)
+        assert np.max(np.abs(got - ref)) <= (1e-12 if dtype == "c128" else c64_tol(k))
+        assert abs(ps - oracle.success_prob(ref, n, marked)) <= (1e-12 if dtype == "c128" else 1e-5)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_bitmask_small_list(B, dtype):
+    n = 11
+    marked = inputs.marked_indices(n, 6, seed=9)
+    mk = B.Marked(n, bitmask=inputs.bitmask(n, marked))
+    st = B.State(n, dtype)
+    st.init_uniform()
+    k = B.grover_optimal_iterations(n, 6)
+    st.iterate(mk, k)
+    got = to_np(st)
+    ref = oracle.grover_operator(oracle.init_uniform(n), n, marked, k)
+    assert np.max(np.abs(got - ref)) <= (1e-11 if dtype == "c128" else c64_tol(k))
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_separate_oracle_and_diffusion(B, dtype):
+    """grover_oracle + grover_diffuse, alternately, equal grover_iterate."""
+    n, k = 10, 9
+    marked = inputs.marked_indices(n, 2, seed=3)
+    psi0 = inputs.gaussian_state(n, seed=4)
+    if dtype == "c64":
+        psi0 = psi0.astype(np.complex64).astype(np.complex128)
+    mk = B.Marked(n, marked)
+    a = B.State(n, dtype)
+    a.init_state(psi0)
+    for _ in range(k):
+        a.oracle(mk)
+        a.diffuse()
+    b = B.State(n, dtype)
+    b.init_state(psi0)
+    b.iterate(mk, k)
+    ga, gb = to_np(a), to_np(b)
+    ref = oracle.grover_operator(psi0.copy(), n, marked, k)
+    tol = 1e-12 if dtype == "c128" else c64_tol(k)
+    assert np.max(np.abs(ga - ref)) <= tol and np.max(np.abs(gb - ref)) <= tol
+    # the diffusion alone is the oracle's inversion about the mean
+    c = B.State(n, dtype)
+    c.init_state(psi0)
+    c.diffuse()
+    assert np.max(np.abs(to_np(c) - oracle.inversion_mean(psi0.copy(), n))) <= (1e-15 if dtype == "c128" else 1e-6)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_edge_marked_sets(B, dtype):
+    n = 9
+    N = 1 << n
+    for marked in ([0], [N - 1], [0, N - 1], list(range(0, N, 4)), []):
+        marked = np.asarray(marked, dtype=np.uint64)
+        m = marked.size
+        k = B.grover_optimal_iterations(n, m) if m else 5
+        mk = B.Marked(n, marked)
+        st = B.State(n, dtype)
+        st.init_uniform()
+        st.iterate(mk, k)
+        got = to_np(st)
+        ref = oracle.grover_operator(oracle.init_uniform(n), n, marked, k)
+        assert np.max(np.abs(got - ref)) <= (1e-12 if dtype == "c128" else c64_tol(k)), marked
+        check_groups(got, marked)
+
+
+def test_measure_probs_bit_exact(B):
+    n = 12
+    marked = inputs.marked_indices(n, 3, seed=1)
+    psi0 = inputs.gaussian_state(n, seed=2)
+    for dtype in ("c128", "c64"):
+        st = B.State(n, dtype)
+        st.init_state(psi0 if dtype == "c128" else psi0.astype(np.complex64))
+        st.iterate(B.Marked(n, marked), 17)
+        got = to_np(st)
+        p = st.measure_probs()
+        assert np.array_equal(p, oracle.probs(got, n))
+        pd = torch.empty(1 << n, dtype=torch.float64, device="cuda")
+        st.measure_probs(pd)
+        torch.cuda.synchronize()
+        assert np.array_equal(pd.cpu().numpy(), p)
+        ps, nrm = st.success_prob(B.Marked(n, marked))
+        assert abs(ps - oracle.success_prob(got, n, marked)) <= 1e-15
+        assert abs(nrm - oracle.norm(got, n)) <= (1e-14 if dtype == "c128" else 1e-7)
+
+
+def test_deterministic(B):
+    n = 18
+    marked = inputs.marked_indices(n, 4, seed=8)
+    mk = B.Marked(n, marked)
+    outs = []
+    for _ in range(2):
+        st = B.State(n, "c64")
+        st.init_state(inputs.gaussian_state(n, seed=3).astype(np.complex64))
+        st.iterate(mk, 33)
+        outs.append(to_np(st))
+    assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("mode", ["fp32", "kahan", "fp64"])
+def test_accumulation_modes(B, mode):
+    n, k = 16, 40
+    marked = inputs.marked_indices(n, 8, seed=31)
+    psi0 = inputs.gaussian_state(n, seed=32).astype(np.complex64).astype(np.complex128)
+    st = B.State(n, "c64")
+    st.set_accum(mode)
+    st.init_state(psi0)
+    st.iterate(B.Marked(n, marked), k)
+    ref = oracle.grover_operator(psi0.copy(), n, marked, k)
+    assert np.max(np.abs(to_np(st) - ref)) <= c64_tol(k)
+
+
+def test_c128_rejects_fp32_accumulation(B):
+    st = B.State(6, "c128")
+    with pytest.raises(B.GroverError):
+        st.set_accum("kahan")
+
+
+def test_invalid_marked_for_state(B):
+    st = B.State(6, "c64")
+    with pytest.raises(B.GroverError):
+        st.iterate(B.Marked(7, [1]), 1)
+    with pytest.raises(B.GroverError):
+        st.measure_topm(17)

@@ -1,0 +1,108 @@
+"""The C-ABI library loads, exports every symbol include/grover.h declares, and
+rejects bad arguments on the host before touching the GPU (CPU only)."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2005_04635_gb300 import binding
+from paper_2005_04635_gb300 import build as gbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "grover.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(gbuild.library_path()):
+        gbuild.build()
+    return binding.lib()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(grover_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_api():
+    names = declared_functions()
+    for must in ("grover_create", "grover_init_uniform", "grover_init_state", "grover_marked_from_list",
+                 "grover_marked_from_bitmask", "grover_oracle", "grover_diffuse", "grover_iterate",
+                 "grover_iterate_gate", "grover_measure_probs", "grover_measure_topm", "grover_success_prob",
+                 "grover_sync", "grover_last_error", "grover_optimal_iterations"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), f"libgrover.so does not export {name}"
+        assert name in binding._SIGS, f"binding has no signature for {name}"
+
+
+def test_status_strings(lib):
+    for code, name in binding.STATUS.items():
+        assert lib.grover_status_string(code).decode() == name
+
+
+def test_optimal_iterations(lib):
+    f = binding.grover_optimal_iterations
+    assert f(3, 1) == 2 and f(12, 1) == 50
+    assert [f(28, m) for m in (1, 4, 16)] == [12867, 6433, 3216]
+    assert f(33, 1) == 72792 and f(26, 8) == 2274
+    assert f(10, 0) == 0 and f(0, 1) == 0 and f(64, 1) == 0
+
+
+def _marked(lib, n, idx):
+    h = ctypes.c_void_p()
+    a = np.ascontiguousarray(np.asarray(idx, dtype=np.uint64))
+    st = lib.grover_marked_from_list(ctypes.byref(h), n, a.ctypes.data if a.size else None, a.size)
+    return st, h
+
+
+def test_marked_list_validation(lib):
+    st, _ = _marked(lib, 4, [3, 1])
+    assert binding.STATUS[st] == "GROVER_EUNSORTED"
+    st, _ = _marked(lib, 4, [1, 1])
+    assert binding.STATUS[st] == "GROVER_EDUP"
+    st, _ = _marked(lib, 4, [1, 16])
+    assert binding.STATUS[st] == "GROVER_ERANGE"
+    assert b"16" in lib.grover_last_error(None)
+    st, _ = _marked(lib, 0, [0])
+    assert binding.STATUS[st] == "GROVER_EINVAL"
+    st, _ = _marked(lib, 34, [0])
+    assert binding.STATUS[st] == "GROVER_EINVAL"
+    assert lib.grover_marked_from_list(None, 4, None, 0) == 1
+    a = np.zeros(1, dtype=np.uint64)
+    assert lib.grover_marked_from_list(ctypes.byref(ctypes.c_void_p()), 4, None, 1) == 1
+
+
+def test_bitmask_validation(lib):
+    h = ctypes.c_void_p()
+    w = np.zeros(3, dtype=np.uint32)
+    st = lib.grover_marked_from_bitmask(ctypes.byref(h), 6, w.ctypes.data, 3, 0)  # 2^6 needs 2 words
+    assert binding.STATUS[st] == "GROVER_ERANGE"
+    st = lib.grover_marked_from_bitmask(ctypes.byref(h), 6, None, 2, 0)
+    assert binding.STATUS[st] == "GROVER_EINVAL"
+
+
+def test_create_validation(lib):
+    h = ctypes.c_void_p()
+    assert lib.grover_create(None, 4, 0, 16, None) == 1
+    assert lib.grover_create(ctypes.byref(h), 4, 0, None, None) == 1  # NULL buffer
+    assert lib.grover_create(ctypes.byref(h), 4, 0, 8, None) == 1  # misaligned
+    assert lib.grover_create(ctypes.byref(h), 34, 0, 16, None) == 1  # n too large for c64
+    assert lib.grover_create(ctypes.byref(h), 33, 1, 16, None) == 1  # n too large for c128
+    assert lib.grover_create(ctypes.byref(h), 4, 7, 16, None) == 1  # bad dtype
+    assert h.value is None
+
+
+def test_null_handles(lib):
+    for fn in ("grover_init_uniform", "grover_diffuse", "grover_sync"):
+        assert getattr(lib, fn)(None) == 1
+    assert lib.grover_iterate(None, None, 1) == 1
+    assert lib.grover_destroy(None) == 0 and lib.grover_marked_destroy(None) == 0
