@@ -179,6 +179,37 @@ grover_status grover_measure_topm(grover_state *s, size_t m, uint64_t *idx, doub
 grover_status grover_success_prob(grover_state *s, const grover_marked *mk,
                                   double *p_success, double *norm);
 
+/* ---- iteration without device allocation -------------------------------- */
+
+/* The paper has no counterpart to this call; it exists for callers that must
+ * not allocate device memory.  grover_create cudaMalloc's a small scratch
+ * area, which some callers cannot do: code running while a framework's caching
+ * allocator owns the device memory budget, loops that cannot take the implicit
+ * device-wide synchronisation of cudaMalloc / cudaFree, or plug-ins that are
+ * only handed device buffers.  This call performs k iterations like
+ * grover_iterate (oracle then inversion about the mean, default accumulation)
+ * on the caller's buffers and allocates nothing.
+ *   dev_amps    device buffer of 2^n amplitudes of dtype, 16-byte aligned,
+ *               updated in place;
+ *   dev_marked  device array of m marked indices, strictly increasing and
+ *               < 2^n (not checked: a list that breaks this gives wrong results
+ *               but no out-of-bounds access); may be NULL when m == 0;
+ *   cuda_stream the stream the work is queued on (asynchronous).
+ * Its scratch (per-block partial sums, the mean, a counter) is a file-scope
+ * device array of 33,280 bytes, which every GPU that loads the library holds
+ * until the process exits; a device that could run more than 2048 blocks of
+ * 256 threads at once is rejected with GROVER_EUNSUPPORTED, and n beyond 33
+ * (complex64) / 32 (complex128) with GROVER_EINVAL (message in
+ * grover_last_error(NULL)).  The first call on a device looks the array's
+ * address up (cudaGetSymbolAddress) with that device current: make that first
+ * call before any stream capture.  All calls on a device share the array and
+ * it keeps the last call's contents (each call resets the counter it needs);
+ * calls that overlap on the GPU -- on different streams, or from host threads
+ * without ordering -- race on it and give wrong results. */
+grover_status grover_iterate_noalloc(void *dev_amps, int n_qubits, grover_dtype dtype,
+                                     const uint64_t *dev_marked, size_t m, uint64_t k,
+                                     void *cuda_stream);
+
 /* ---- synchronisation and errors ----------------------------------------- */
 
 /* Waits for the handle's stream and reads the device status word:

@@ -43,6 +43,7 @@ _SIGS = {
     "grover_measure_probs": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
     "grover_measure_topm": (ctypes.c_int, [_vp, ctypes.c_size_t, _vp, _vp]),
     "grover_success_prob": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "grover_iterate_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t, ctypes.c_uint64, _vp]),
     "grover_sync": (ctypes.c_int, [_vp]),
     "grover_last_error": (ctypes.c_char_p, [_vp]),
     "grover_status_string": (ctypes.c_char_p, [ctypes.c_int]),

@@ -114,6 +114,8 @@ grover_status ensure_mean(grover_state *s, const MarkedDev &mk, uint64_t key) {
 
 }  // namespace
 
+void grv::set_thread_error(const char *msg) { snprintf(g_err, sizeof g_err, "%s", msg); }
+
 extern "C" {
 
 const char *grover_status_string(grover_status st) {

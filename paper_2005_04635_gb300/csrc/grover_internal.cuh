@@ -97,6 +97,10 @@ cudaError_t launch_norm_success(const void *amps, int n, grover_dtype dt, const 
 cudaError_t launch_topm(const void *amps, int n, grover_dtype dt, int m, Scratch &sc,
                         cudaStream_t st, const Geometry &g);
 
+// ---- errors (grover_api.cu) ------------------------------------------------
+// Sets the message grover_last_error(NULL) returns on this host thread.
+void set_thread_error(const char *msg);
+
 }  // namespace grv
 
 // Handle layout (opaque in the C ABI).
