@@ -57,21 +57,28 @@ typedef enum { GROVER_C64 = 0, GROVER_C128 = 1 } grover_dtype;
 
 /* How the complex mean <c> is accumulated (section "Inversion About Mean
  * Operator"; the paper sums Re and Im separately in one running sum).  Every
- * mode combines the per-block partial sums in FP64 in a fixed order, so a
- * result is bitwise reproducible run to run.
- *   GROVER_ACC_DEFAULT: GROVER_ACC_FP64.
+ * mode combines per-block partial sums in a fixed order, so a result is
+ * bitwise reproducible run to run.
+ *   GROVER_ACC_DEFAULT: complex64: GROVER_ACC_FP64; complex128: GROVER_ACC_EXACT.
  *   GROVER_ACC_FP32:    complex64 only; plain FP32 running sum per thread and an
- *                       FP32 tree across the block.
+ *                       FP32 tree across the block, FP64 across blocks.
  *   GROVER_ACC_KAHAN:   complex64 only; Neumaier-compensated FP32 running sum
- *                       per thread and an FP32 tree across the block.
- *   GROVER_ACC_FP64:    complex64: FP32 sum of each thread's 2..8 amplitudes
- *                       per load group, FP64 above that; complex128: FP64
- *                       throughout. */
+ *                       per thread and an FP32 tree across the block, FP64
+ *                       across blocks.
+ *   GROVER_ACC_FP64:    complex64: FP32 pairwise sum of each thread's 8
+ *                       amplitudes per load group, FP64 above that;
+ *                       complex128: FP64 throughout.
+ *   GROVER_ACC_EXACT:   every amplitude of magnitude below 1 is added exactly as
+ *                       a fixed-point integer with 100 fractional bits (larger
+ *                       magnitudes in FP64); threads and blocks are combined in
+ *                       double-double.  The sum is exact up to 2^-100 per
+ *                       amplitude and a final double-double rounding. */
 typedef enum {
     GROVER_ACC_DEFAULT = 0,
     GROVER_ACC_FP32 = 1,
     GROVER_ACC_KAHAN = 2,
-    GROVER_ACC_FP64 = 3
+    GROVER_ACC_FP64 = 3,
+    GROVER_ACC_EXACT = 4
 } grover_accum;
 
 typedef struct grover_state grover_state;   /* opaque: n, dtype, buffer, stream, scratch, cached mean */
@@ -187,7 +194,7 @@ grover_status grover_success_prob(grover_state *s, const grover_marked *mk,
  * allocator owns the device memory budget, loops that cannot take the implicit
  * device-wide synchronisation of cudaMalloc / cudaFree, or plug-ins that are
  * only handed device buffers.  This call performs k iterations like
- * grover_iterate (oracle then inversion about the mean, default accumulation)
+ * grover_iterate (oracle then inversion about the mean, GROVER_ACC_FP64 sums)
  * on the caller's buffers and allocates nothing.
  *   dev_amps    device buffer of 2^n amplitudes of dtype, 16-byte aligned,
  *               updated in place;

@@ -21,7 +21,7 @@ GROVER_OK = 0
 STATUS = {0: "GROVER_OK", 1: "GROVER_EINVAL", 2: "GROVER_ENOMEM", 3: "GROVER_ECUDA", 4: "GROVER_ETIMEOUT",
           5: "GROVER_EUNSORTED", 6: "GROVER_EDUP", 7: "GROVER_ERANGE", 8: "GROVER_EUNSUPPORTED"}
 C64, C128 = 0, 1
-ACC = {"default": 0, "fp32": 1, "kahan": 2, "fp64": 3}
+ACC = {"default": 0, "fp32": 1, "kahan": 2, "fp64": 3, "exact": 4}
 
 # every symbol include/grover.h declares, with its ctypes signature
 _vp = ctypes.c_void_p

@@ -217,7 +217,7 @@ grover_status grover_destroy(grover_state *s) {
 
 grover_status grover_set_accum(grover_state *s, grover_accum mode) {
     if (grover_status st = check_state(s)) return st;
-    if (mode < GROVER_ACC_DEFAULT || mode > GROVER_ACC_FP64)
+    if (mode < GROVER_ACC_DEFAULT || mode > GROVER_ACC_EXACT)
         return fail(s, GROVER_EINVAL, "unknown accumulation mode %d", (int)mode);
     if (s->dtype == GROVER_C128 && (mode == GROVER_ACC_FP32 || mode == GROVER_ACC_KAHAN))
         return fail(s, GROVER_EINVAL, "FP32 accumulation modes apply to complex64 states only");

@@ -59,6 +59,8 @@ __global__ void __launch_bounds__(kThreads) k_probs(const T *amps, uint64_t firs
 // ---- norm and success probability --------------------------------------------------
 // complex64 squares are formed in FP32 per 16-byte vector and accumulated in
 // FP64 above that; complex128 squares and sums are FP64.
+constexpr int kMUnroll = 4;
+
 template <class T, bool BITS>
 __global__ void __launch_bounds__(kThreads)
 k_norm_success(const T *amps, uint64_t nvec, const uint32_t *words, double2 *partials, unsigned *ticket,
@@ -66,22 +68,38 @@ k_norm_success(const T *amps, uint64_t nvec, const uint32_t *words, double2 *par
     using V = typename Vec<T>::V;
     constexpr int APV = Vec<T>::APV;
     const V *v = reinterpret_cast<const V *>(amps);
+    const uint64_t tile = (uint64_t)kThreads * kMUnroll;
     double nrm = 0.0, suc = 0.0;
-    for (uint64_t i = (uint64_t)blockIdx.x * kThreads + threadIdx.x; i < nvec; i += (uint64_t)gridDim.x * kThreads) {
-        const V c = v[i];
+    for (uint64_t base = (uint64_t)blockIdx.x * tile; base < nvec; base += (uint64_t)gridDim.x * tile) {
+        V c[kMUnroll];
+#pragma unroll
+        for (int u = 0; u < kMUnroll; ++u) {
+            const uint64_t i = base + (uint64_t)u * kThreads + threadIdx.x;
+            if (i < nvec) c[u] = __ldcs(v + i);
+        }
         if constexpr (APV == 2) {
-            const float p0 = fmaf(c.x, c.x, c.y * c.y);
-            const float p1 = fmaf(c.z, c.z, c.w * c.w);
-            nrm += (double)(p0 + p1);
-            if (BITS) {
-                const uint32_t w = words[(i * 2) >> 5] >> (uint32_t)((i * 2) & 31);
-                if (w & 1u) suc += sq(c.x, c.y);
-                if (w & 2u) suc += sq(c.z, c.w);
+            // squares in FP32, the 8 of one tile summed pairwise, FP64 above
+            float q[kMUnroll];
+#pragma unroll
+            for (int u = 0; u < kMUnroll; ++u) {
+                const uint64_t i = base + (uint64_t)u * kThreads + threadIdx.x;
+                q[u] = i < nvec ? fmaf(c[u].x, c[u].x, c[u].y * c[u].y) + fmaf(c[u].z, c[u].z, c[u].w * c[u].w) : 0.f;
+                if (BITS && i < nvec) {
+                    const uint32_t w = words[(i * 2) >> 5] >> (uint32_t)((i * 2) & 31);
+                    if (w & 1u) suc += sq(c[u].x, c[u].y);
+                    if (w & 2u) suc += sq(c[u].z, c[u].w);
+                }
             }
+            nrm += (double)((q[0] + q[1]) + (q[2] + q[3]));
         } else {
-            const double p = sq(c.x, c.y);
-            nrm += p;
-            if (BITS && ((words[i >> 5] >> (uint32_t)(i & 31)) & 1u)) suc += p;
+#pragma unroll
+            for (int u = 0; u < kMUnroll; ++u) {
+                const uint64_t i = base + (uint64_t)u * kThreads + threadIdx.x;
+                if (i >= nvec) continue;
+                const double p = sq(c[u].x, c[u].y);
+                nrm += p;
+                if (BITS && ((words[i >> 5] >> (uint32_t)(i & 31)) & 1u)) suc += p;
+            }
         }
     }
     __shared__ double sm[kThreads / 32];
@@ -138,8 +156,9 @@ template <int K> struct TopK {
             i[j] = ~0ull;
         }
     }
-    __device__ __forceinline__ void insert(double pv, uint64_t iv) {
-        if (!better(pv, iv, p[K - 1], i[K - 1])) return;
+    // returns false when (pv, iv) does not enter the list
+    __device__ __forceinline__ bool insert(double pv, uint64_t iv) {
+        if (!better(pv, iv, p[K - 1], i[K - 1])) return false;
         p[K - 1] = pv;
         i[K - 1] = iv;
 #pragma unroll
@@ -153,6 +172,7 @@ template <int K> struct TopK {
                 i[j - 1] = ti;
             }
         }
+        return true;
     }
     // FP32 prefilter bound: a value whose FP32 estimate is below it cannot
     // enter the list (the estimate is within 2^-22 of the exact square).
@@ -232,19 +252,39 @@ k_topm(const T *amps, uint64_t nvec, Cand *cand, unsigned *ticket, Cand *final_o
     const V *v = reinterpret_cast<const V *>(amps);
     TopK<K> t;
     t.init();
+    // A thread visits indices in increasing order, so an amplitude equal to one
+    // that already failed to enter can never enter later (its probability ties
+    // and its index is larger): equal magnitudes are skipped by comparing bits.
     float b32 = -1.0f;
+    uint64_t seen_hi = ~0ull, seen_lo = ~0ull;
     for (uint64_t i = (uint64_t)blockIdx.x * kThreads + threadIdx.x; i < nvec; i += (uint64_t)gridDim.x * kThreads) {
-        const V c = v[i];
+        const V c = __ldcs(v + i);
         if constexpr (APV == 2) {
             const float e0 = fmaf(c.x, c.x, c.y * c.y);
             const float e1 = fmaf(c.z, c.z, c.w * c.w);
-            if (e0 >= b32 || e1 >= b32) {
-                t.insert(sq(c.x, c.y), 2 * i);
-                t.insert(sq(c.z, c.w), 2 * i + 1);
-                b32 = t.bound32();
+            if (e0 >= b32) {
+                const uint64_t key = ((uint64_t)(__float_as_uint(c.x) & 0x7fffffffu) << 32) | (__float_as_uint(c.y) & 0x7fffffffu);
+                if (key != seen_lo) {
+                    if (!t.insert(sq(c.x, c.y), 2 * i)) seen_lo = key;
+                    b32 = t.bound32();
+                }
+            }
+            if (e1 >= b32) {
+                const uint64_t key = ((uint64_t)(__float_as_uint(c.z) & 0x7fffffffu) << 32) | (__float_as_uint(c.w) & 0x7fffffffu);
+                if (key != seen_lo) {
+                    if (!t.insert(sq(c.z, c.w), 2 * i + 1)) seen_lo = key;
+                    b32 = t.bound32();
+                }
             }
         } else {
-            t.insert(sq(c.x, c.y), i);
+            const uint64_t kh = (uint64_t)__double_as_longlong(c.x) & 0x7fffffffffffffffull;
+            const uint64_t kl = (uint64_t)__double_as_longlong(c.y) & 0x7fffffffffffffffull;
+            if (kh != seen_hi || kl != seen_lo) {
+                if (!t.insert(sq(c.x, c.y), i)) {
+                    seen_hi = kh;
+                    seen_lo = kl;
+                }
+            }
         }
     }
     block_merge<K>(t, cand + (size_t)blockIdx.x * K);

@@ -136,16 +136,18 @@ extern "C" grover_status grover_iterate_noalloc(void *dev_amps, int n, grover_dt
     a.inv_n = ldexp(1.0, -n);
     a.stream_hint = (long long)(N * (dtype == GROVER_C64 ? 8 : 16)) > geo.l2_bytes / 2;
 
-    // mean of O c for the first iteration, then k fused passes
+    // mean of O c for the first iteration, then k fused passes; FP64
+    // accumulation keeps one partial-sum slot per CTA
+    const grover_accum acc = GROVER_ACC_FP64;
     a.mu_in = mu;
     a.mu_out = mu;
-    if ((e = launch_reduce(a, dtype, GROVER_ACC_DEFAULT, stream, geo)) != cudaSuccess)
+    if ((e = launch_reduce(a, dtype, acc, stream, geo)) != cudaSuccess)
         return noalloc_fail(GROVER_ECUDA, "mean reduction launch", e);
     int slot = 0;
     for (uint64_t t = 0; t < k; ++t) {
         a.mu_in = mu + slot;
         a.mu_out = mu + (slot ^ 1);
-        if ((e = launch_pass(a, dtype, GROVER_ACC_DEFAULT, stream, geo)) != cudaSuccess)
+        if ((e = launch_pass(a, dtype, acc, stream, geo)) != cudaSuccess)
             return noalloc_fail(GROVER_ECUDA, "iteration pass launch", e);
         slot ^= 1;
     }

@@ -172,8 +172,76 @@ struct AccKahan {
     }
 };
 
+// GROVER_ACC_EXACT: magnitudes below 1 are added exactly as 128-bit integers
+// in units of 2^-100 (bits below 2^-100 are dropped: < 2^-100 per amplitude),
+// on the integer pipe; larger magnitudes, Inf and NaN go to an FP64 side sum.
+// A thread's integer sum stays below 2^115 for any 2^32 amplitudes.
+constexpr int kFixLsb = 100;
+__device__ __forceinline__ void fix_add(unsigned __int128 &acc, double &side, double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned e = (unsigned)(b >> 52) & 0x7FFu;
+    if (e >= 1023u) {
+        side += x;
+        return;
+    }
+    const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | ((unsigned long long)(e != 0u) << 52);
+    const int sh = (int)e - (1075 - kFixLsb);  // x = m * 2^(sh - kFixLsb)
+    unsigned __int128 v;
+    if (sh >= 0) v = (unsigned __int128)m << sh;
+    else v = sh > -64 ? (unsigned __int128)(m >> (-sh)) : (unsigned __int128)0;
+    const unsigned __int128 neg = (unsigned __int128)(__int128)((long long)b >> 63);
+    acc += (v ^ neg) - neg;
+}
+__device__ __forceinline__ void fix_add(unsigned __int128 &acc, double &side, float x) {
+    const unsigned b = __float_as_uint(x);
+    const unsigned e = (b >> 23) & 0xFFu;
+    if (e >= 127u) {
+        side += (double)x;
+        return;
+    }
+    const unsigned long long m = (b & 0x7FFFFFu) | ((unsigned)(e != 0u) << 23);
+    const int sh = (int)e - (150 - kFixLsb);
+    unsigned __int128 v;
+    if (sh >= 0) v = (unsigned __int128)m << sh;
+    else v = sh > -24 ? (unsigned __int128)(m >> (-sh)) : (unsigned __int128)0;
+    const unsigned __int128 neg = (unsigned __int128)(__int128)((int)b >> 31);
+    acc += (v ^ neg) - neg;
+}
+struct AccX {
+    unsigned __int128 r = 0, i = 0;
+    double side_r = 0.0, side_i = 0.0;
+    template <int G, class T> __device__ __forceinline__ void add_group(const T *re, const T *im) {
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            fix_add(r, side_r, re[j]);
+            fix_add(i, side_i, im[j]);
+        }
+    }
+};
+
+// double-double arithmetic for combining exact per-thread sums (plain adds only)
+struct DD {
+    double h, l;
+};
+__device__ __forceinline__ DD dd_add(DD a, DD b) {
+    const double s = __dadd_rn(a.h, b.h);
+    const double bb = __dsub_rn(s, a.h);
+    double e = __dadd_rn(__dsub_rn(a.h, __dsub_rn(s, bb)), __dsub_rn(b.h, bb));
+    e = __dadd_rn(e, __dadd_rn(a.l, b.l));
+    const double h = __dadd_rn(s, e);
+    return DD{h, __dsub_rn(e, __dsub_rn(h, s))};
+}
+__device__ __forceinline__ DD dd_from_fix(unsigned __int128 u, double side) {
+    const __int128 x = (__int128)u;
+    const double h = (double)x;
+    const double l = (double)(x - (__int128)h);
+    return dd_add(DD{h * 0x1p-100, l * 0x1p-100}, DD{side, 0.0});
+}
+
 template <class T, int ACC> struct AccSel;
 template <int ACC> struct AccSel<double, ACC> { using A = AccD; using S = double; };
+template <> struct AccSel<double, GROVER_ACC_EXACT> { using A = AccX; using S = double; };
+template <> struct AccSel<float, GROVER_ACC_EXACT> { using A = AccX; using S = double; };
 template <> struct AccSel<float, GROVER_ACC_FP64> { using A = AccF64; using S = double; };
 template <> struct AccSel<float, GROVER_ACC_FP32> { using A = AccF32; using S = float; };
 template <> struct AccSel<float, GROVER_ACC_KAHAN> { using A = AccKahan; using S = float; };
@@ -228,6 +296,53 @@ __device__ __forceinline__ void grid_combine(double2 part, const PassArgs &a) {
     si = block_sum(si, sm);
     if (threadIdx.x == 0) {
         *a.mu_out = make_double2(sr * a.inv_n, si * a.inv_n);
+        *a.ticket = 0u;
+    }
+}
+
+__device__ __forceinline__ DD warp_dd(DD v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = dd_add(v, DD{__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)});
+    return v;
+}
+__device__ __forceinline__ DD block_dd(DD v, DD *sm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = warp_dd(v);
+    __syncthreads();
+    if (lane == 0) sm[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        v = (lane < kThreads / 32) ? sm[lane] : DD{0.0, 0.0};
+        v = warp_dd(v);
+    }
+    return v;
+}
+// Exact mode: per-CTA double-double partials in partials[2b], partials[2b+1];
+// the last CTA adds them in a fixed order in double-double.
+__device__ __forceinline__ void grid_combine_dd(DD re, DD im, const PassArgs &a) {
+    __shared__ DD sm[kThreads / 32];
+    __shared__ unsigned s_last;
+    if (threadIdx.x == 0) {
+        a.partials[2 * blockIdx.x] = make_double2(re.h, re.l);
+        a.partials[2 * blockIdx.x + 1] = make_double2(im.h, im.l);
+        __threadfence();
+        unsigned t = atomicAdd(a.ticket, 1u);
+        s_last = (t == gridDim.x - 1) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    DD sr{0.0, 0.0}, si{0.0, 0.0};
+    for (unsigned j = threadIdx.x; j < gridDim.x; j += kThreads) {
+        const double2 qr = __ldcg(a.partials + 2 * j), qi = __ldcg(a.partials + 2 * j + 1);
+        sr = dd_add(sr, DD{qr.x, qr.y});
+        si = dd_add(si, DD{qi.x, qi.y});
+    }
+    sr = block_dd(sr, sm);
+    si = block_dd(si, sm);
+    if (threadIdx.x == 0) {
+        *a.mu_out = make_double2(__dadd_rn(sr.h, sr.l) * a.inv_n, __dadd_rn(si.h, si.l) * a.inv_n);
         *a.ticket = 0u;
     }
 }
@@ -326,12 +441,19 @@ __global__ void __launch_bounds__(kThreads) k_pass(PassArgs a) {
         acc.template add_group<G>(gr, gi);
     }
 
-    // block tree in S precision, then FP64 partial
-    __shared__ S sm[kThreads / 32];
-    const auto val = acc_value(acc);
-    S r = block_sum((S)val.x, sm);
-    S im = block_sum((S)val.y, sm);
-    grid_combine(make_double2((double)r, (double)im), a);
+    if constexpr (ACC == GROVER_ACC_EXACT) {
+        __shared__ DD smd[kThreads / 32];
+        const DD r = block_dd(dd_from_fix(acc.r, acc.side_r), smd);
+        const DD im = block_dd(dd_from_fix(acc.i, acc.side_i), smd);
+        grid_combine_dd(r, im, a);
+    } else {
+        // block tree in S precision, then FP64 partial
+        __shared__ S sm[kThreads / 32];
+        const auto val = acc_value(acc);
+        S r = block_sum((S)val.x, sm);
+        S im = block_sum((S)val.y, sm);
+        grid_combine(make_double2((double)r, (double)im), a);
+    }
 }
 
 // ---- initialisation / oracle -----------------------------------------------------------------
@@ -455,10 +577,16 @@ cudaError_t dispatch_mark(const PassArgs &a, cudaStream_t st, const Geometry &g)
 
 template <bool UPDATE>
 cudaError_t dispatch(const PassArgs &a, grover_dtype dt, grover_accum acc, cudaStream_t st, const Geometry &g) {
-    if (dt == GROVER_C128) return dispatch_mark<double, GROVER_ACC_FP64, UPDATE>(a, st, g);
+    if (dt == GROVER_C128) {
+        // complex128 default: exact integer accumulation (the FP64 pipe is the
+        // bottleneck of the pass otherwise)
+        if (acc == GROVER_ACC_FP64) return dispatch_mark<double, GROVER_ACC_FP64, UPDATE>(a, st, g);
+        return dispatch_mark<double, GROVER_ACC_EXACT, UPDATE>(a, st, g);
+    }
     switch (acc) {
     case GROVER_ACC_FP32: return dispatch_mark<float, GROVER_ACC_FP32, UPDATE>(a, st, g);
     case GROVER_ACC_KAHAN: return dispatch_mark<float, GROVER_ACC_KAHAN, UPDATE>(a, st, g);
+    case GROVER_ACC_EXACT: return dispatch_mark<float, GROVER_ACC_EXACT, UPDATE>(a, st, g);
     default: return dispatch_mark<float, GROVER_ACC_FP64, UPDATE>(a, st, g);
     }
 }

@@ -212,7 +212,7 @@ def test_deterministic(B):
     assert np.array_equal(outs[0], outs[1])
 
 
-@pytest.mark.parametrize("mode", ["fp32", "kahan", "fp64"])
+@pytest.mark.parametrize("mode", ["fp32", "kahan", "fp64", "exact"])
 def test_accumulation_modes(B, mode):
     n, k = 16, 40
     marked = inputs.marked_indices(n, 8, seed=31)
@@ -223,6 +223,51 @@ def test_accumulation_modes(B, mode):
     st.iterate(B.Marked(n, marked), k)
     ref = oracle.grover_operator(psi0.copy(), n, marked, k)
     assert np.max(np.abs(to_np(st) - ref)) <= c64_tol(k)
+
+
+def test_c128_fp64_accumulation(B):
+    n, k = 15, 120
+    marked = inputs.marked_indices(n, 2, seed=51)
+    psi0 = inputs.gaussian_state(n, seed=52)
+    st = B.State(n, "c128")
+    st.set_accum("fp64")
+    st.init_state(psi0)
+    st.iterate(B.Marked(n, marked), k)
+    ref = oracle.grover_operator(psi0.copy(), n, marked, k)
+    assert np.max(np.abs(to_np(st) - ref)) <= 1e-12
+
+
+@pytest.mark.parametrize("dtype,mode", [("c128", "exact"), ("c128", "fp64"), ("c64", "exact"), ("c64", "fp64")])
+def test_mean_rounding(B, dtype, mode):
+    """An amplitude that is exactly 0 becomes exactly 2<c> after one diffusion,
+    which exposes the computed mean.  Exact mode: the correctly rounded mean, to
+    one unit in the last place.  FP64 mode: the recursive-summation bound
+    |S_hat - S| <= gamma_L * sum|x| (L additions per term, unit roundoff u), which
+    holds for any summation order: complex128 L = N - 1, u = 2^-53; complex64
+    L = 7 in FP32 (u = 2^-24, pairwise tile of 8) plus N/8 in FP64."""
+    import math
+    n = 16
+    N = 1 << n
+    psi0 = inputs.gaussian_state(n, seed=61) * 3.0
+    if dtype == "c64":
+        psi0 = psi0.astype(np.complex64).astype(np.complex128)
+    psi0[5] = 0.0
+    st = B.State(n, dtype)
+    st.set_accum(mode)
+    st.init_state(psi0)
+    st.diffuse()
+    got = to_np(st)[5]
+    for part, g in ((psi0.real, got.real), (psi0.imag, got.imag)):
+        exact = 2.0 * math.fsum(part.tolist()) / N  # fsum: correctly rounded sum
+        sum_abs = 2.0 * float(np.sum(np.abs(part))) / N
+        if dtype == "c128":
+            ulp = np.spacing(abs(exact))
+            bound = ulp if mode == "exact" else ulp + (N - 1) * 2.0 ** -53 * sum_abs
+        else:
+            exact = float(np.float32(exact))
+            ulp = float(np.spacing(np.float32(abs(exact))))
+            bound = ulp if mode == "exact" else ulp + (7 * 2.0 ** -24 + (N / 8) * 2.0 ** -53) * sum_abs
+        assert abs(g - exact) <= bound, (mode, abs(g - exact), bound)
 
 
 def test_c128_rejects_fp32_accumulation(B):
