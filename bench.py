@@ -41,6 +41,11 @@ WORKLOADS = {
     "n26-c64-m8-k3000": (26, "c64", 8, 3000, 2608),
     "n24-c64-m1-k200": (24, "c64", 1, 200, 2401),
     "n26-c64-m1-k20": (26, "c64", 1, 20, 2621),
+    "n12-c128-m1": (12, "c128", 1, None, 1201),
+    "n16-c64-m1": (16, "c64", 1, None, 1601),
+    "n18-c64-m1": (18, "c64", 1, None, 1801),
+    "n17-c128-m1": (17, "c128", 1, None, 1711),
+    "n20-c64-m1": (20, "c64", 1, None, 2001),
     "n26-c128-m1-k10": (26, "c128", 1, 10, 2631),
 }
 DEFAULT_WORKLOAD = "n33-c64-m1-k100"
@@ -62,11 +67,12 @@ def describe(w):
             f"indices, uniform init, {w['k']} iterations + init + measure per step")
 
 
-def config_of(w, n_gpus):
+def config_of(w, n_gpus, path="auto"):
     state_bytes = (1 << w["n"]) * BYTES_PER_AMP[w["dtype"]]
+    l2 = (f"inputs larger than L2 ({state_bytes / 2**30:.1f} GiB state, 129 MB L2)" if state_bytes > 129e6 else
+          f"state of {state_bytes / 2**20:.2f} MiB stays on chip / in L2 by design (small-state workload)")
     return {"workload": describe(w), "name": w["name"], "n": w["n"], "state_dtype": w["dtype"], "M": w["M"],
-            "k": w["k"], "seed": w["seed"], "state_bytes": state_bytes,
-            "l2": f"inputs larger than L2 ({state_bytes / 2**30:.1f} GiB state, 129 MB L2)",
+            "k": w["k"], "seed": w["seed"], "state_bytes": state_bytes, "l2": l2, "path": path,
             "parallelism": f"replicas x{n_gpus}"}
 
 
@@ -215,6 +221,7 @@ def run_ours(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
     st = binding.State(n, dtype, device=dev, stream=stream)
+    st.set_resident({"auto": -1, "pass": 0, "resident": 1}[args.path])
     mk = binding.Marked(n, marked)
 
     ev_it = []
@@ -274,8 +281,32 @@ def run_ours(args):
     e2e_elapsed = time.perf_counter() - t0
     e2e_t, e2e_units = aggregate(e2e_elapsed, float(N) * k * e2e_steps, backend_device=dev)
 
+    # the conventional circuit on the same state, for the speedup of the
+    # equivalent operator over it (a few iterations; not part of `value`)
+    gate = None
+    if args.gate_iters > 0:
+        st.init_uniform()
+        st.iterate_gate(mk, 1)  # warm-up
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        st.iterate_gate(mk, args.gate_iters)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        gate_s = g0.elapsed_time(g1) / 1e3 / args.gate_iters
+        passes = 2 * ((n + 7) // 8)
+        gate = {"iterations_timed": args.gate_iters, "iteration_ms": gate_s * 1e3,
+                "value": N / gate_s, "unit": UNIT, "passes_per_iteration": passes,
+                "hbm_gbs": passes * 2 * BYTES_PER_AMP[dtype] * N / gate_s / 1e9,
+                "engine": "Walsh-Hadamard butterflies, CUDA cores",
+                "operator_speedup": gate_s / pass_s}
+
     if rank != 0:
         return None
+    # the library's choice of the persistent on-chip iterator (grover.h,
+    # GROVER_OPT_RESIDENT)
+    resident = (args.path == "auto" and n <= (17 if dtype == "c64" else 15)) or \
+        (args.path == "resident" and n <= (18 if dtype == "c64" else 17))
     peaks, peak_src = measured_peaks()
     achieved = BYTES_PER_AMP[dtype] * 2 * N / pass_s / 1e9
     traffic = recorded_traffic(w)
@@ -284,17 +315,20 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if dtype == "c64" else "f64",
         "data": "synthetic (seeded marked indices, uniform initial state)",
-        "config": config_of(w, world),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                     "kernel": "k_pass (fused oracle + inversion about the mean + next-mean partial sums)",
-                     "algorithmic_bytes_per_launch": BYTES_PER_AMP[dtype] * 2 * N,
-                     "avg_launch_ms": pass_s * 1e3, "peak_source": f"{peak_src} hbm_gbs"},
+        "config": config_of(w, world, args.path),
+        "roofline": None if resident else {
+            "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+            "kernel": "k_pass (fused oracle + inversion about the mean + next-mean partial sums)",
+            "algorithmic_bytes_per_launch": BYTES_PER_AMP[dtype] * 2 * N,
+            "avg_launch_ms": pass_s * 1e3, "peak_source": f"{peak_src} hbm_gbs"},
+        "iteration_us": pass_s * 1e6,
         "e2e": {"value": e2e_units / e2e_t, "unit": UNIT, "h2d_bytes_per_step": 8 * M,
                 "d2h_bytes_per_step": 16 * min(M, 16) + 16, "steps": e2e_steps},
-        "gpu_launches": args.steps * (k + 5),
+        "gpu_launches": args.steps * ((1 if resident else k + 1) + 4),
         "clocks": clk,
         "result_check": {"p_success": ps, "norm": nrm, "top": [int(x) for x in idx]},
+        "gate_path": gate,
     }
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
@@ -337,6 +371,10 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--gate-iters", type=int, default=2,
+                    help="iterations of the conventional circuit timed for comparison (0: skip)")
+    ap.add_argument("--path", choices=["auto", "pass", "resident"], default="auto",
+                    help="auto: persistent on-chip iterator for small states, else one pass per iteration")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

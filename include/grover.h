@@ -103,6 +103,25 @@ grover_status grover_destroy(grover_state *s);
  * GROVER_EINVAL for FP32/KAHAN on a complex128 state. */
 grover_status grover_set_accum(grover_state *s, grover_accum mode);
 
+typedef enum {
+    /* How grover_iterate runs.  The persistent on-chip iterator keeps the
+     * state in one thread-block cluster's shared memory for all k iterations;
+     * it can run when the state fits (16 CTAs x 200 KiB: n <= 18 complex64,
+     * n <= 17 complex128) and the accumulation mode is GROVER_ACC_DEFAULT or
+     * GROVER_ACC_EXACT, and it sums exactly (fixed point).
+     *   -1 (default): the persistent iterator for n <= 17 (complex64) or
+     *                 n <= 15 (complex128), where it is faster, else one fused
+     *                 pass per iteration;
+     *    0: always one fused pass per iteration;
+     *    1: the persistent iterator wherever it can run (grover_iterate returns
+     *       GROVER_EUNSUPPORTED where it cannot). */
+    GROVER_OPT_RESIDENT = 0
+} grover_option;
+
+/* Sets an execution option of the handle (see grover_option).  GROVER_EINVAL
+ * for an unknown option or value. */
+grover_status grover_set_option(grover_state *s, grover_option opt, int64_t value);
+
 /* ---- state preparation ------------------------------------------------- */
 
 /* psi = H^{(x)n}|0...0>, written directly as c_i = 1/sqrt(N) rounded to the
@@ -156,10 +175,13 @@ grover_status grover_diffuse(grover_state *s);
 grover_status grover_iterate(grover_state *s, const grover_marked *mk, uint64_t k);
 
 /* k iterations of the conventional circuit (section "Background",
- * conventional grover_search): oracle, H^{(x)n}, 2|0><0| - I, H^{(x)n}, with
- * H^{(x)n} applied as blocked Walsh-Hadamard tiles on the tensor cores.  The
- * result equals grover_iterate's up to rounding (no global phase).
- * GROVER_EUNSUPPORTED where this build has no gate path for the dtype / n. */
+ * conventional grover_search): oracle, H^{(x)n}, 2|0><0| - I, H^{(x)n}.
+ * H^{(x)n} is a product of Walsh-Hadamard transforms on groups of up to 8
+ * index bits, one read + write pass over the state per group, with +-1
+ * butterflies and exact power-of-two scaling (2^-n per iteration in total);
+ * the phase shift is fused into the last pass of the first transform.  The
+ * result equals grover_iterate's up to rounding (no global phase).  Invalidates
+ * the cached mean. */
 grover_status grover_iterate_gate(grover_state *s, const grover_marked *mk, uint64_t k);
 
 /* floor(pi/4 * sqrt(2^n / m)), the iteration count that maximises the success

@@ -29,6 +29,7 @@ _SIGS = {
     "grover_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, _vp, _vp]),
     "grover_destroy": (ctypes.c_int, [_vp]),
     "grover_set_accum": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "grover_set_option": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int64]),
     "grover_init_uniform": (ctypes.c_int, [_vp]),
     "grover_init_state": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
     "grover_marked_from_list": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, _vp, ctypes.c_size_t]),
@@ -147,6 +148,10 @@ class State:
     # -- calls with the C names -------------------------------------------------------
     def set_accum(self, mode: str):
         _check(lib().grover_set_accum(self.handle, ACC[mode]), self.handle)
+
+    def set_resident(self, value: int):
+        """-1 automatic, 0 one pass per iteration, 1 the persistent on-chip iterator."""
+        _check(lib().grover_set_option(self.handle, 0, int(value)), self.handle)
 
     def init_uniform(self):
         _check(lib().grover_init_uniform(self.handle), self.handle)

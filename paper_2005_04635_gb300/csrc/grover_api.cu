@@ -57,7 +57,7 @@ Layout scratch_layout() {
     Layout L;
     size_t off = 0;
     L.partials = off; off += align256(sizeof(double2) * kMaxGrid);
-    L.mu = off; off += align256(sizeof(double2) * 2);
+    L.mu = off; off += align256(sizeof(MeanSlot) * 2);
     L.ticket = off; off += align256(sizeof(unsigned));
     L.status = off; off += align256(sizeof(int));
     L.cand = off; off += align256(sizeof(Cand) * (size_t)(kTopMGrid + 1) * kTopMMax);
@@ -190,12 +190,13 @@ grover_status grover_create(grover_state **out, int n, grover_dtype dtype, void 
     }
     s->scratch_base = base;
     s->sc.partials = (double2 *)(base + L.partials);
-    s->sc.mu = (double2 *)(base + L.mu);
+    s->sc.mu = (MeanSlot *)(base + L.mu);
     s->sc.ticket = (unsigned *)(base + L.ticket);
     s->sc.status = (int *)(base + L.status);
     s->sc.cand = (Cand *)(base + L.cand);
     s->sc.red = (double2 *)(base + L.red);
     s->sc.probs_tmp = nullptr;
+    s->resident = -1;
     s->mu_slot = 0;
     s->mu_valid = false;
     s->mu_key = 0;
@@ -223,6 +224,14 @@ grover_status grover_set_accum(grover_state *s, grover_accum mode) {
         return fail(s, GROVER_EINVAL, "FP32 accumulation modes apply to complex64 states only");
     if (mode != s->acc) s->mu_valid = false;
     s->acc = mode;
+    return GROVER_OK;
+}
+
+grover_status grover_set_option(grover_state *s, grover_option opt, int64_t value) {
+    if (grover_status st = check_state(s)) return st;
+    if (opt != GROVER_OPT_RESIDENT) return fail(s, GROVER_EINVAL, "unknown option %d", (int)opt);
+    if (value < -1 || value > 1) return fail(s, GROVER_EINVAL, "GROVER_OPT_RESIDENT takes -1, 0 or 1");
+    s->resident = (int)value;
     return GROVER_OK;
 }
 
@@ -377,6 +386,37 @@ grover_status grover_iterate(grover_state *s, const grover_marked *mk, uint64_t 
     if (grover_status st = check_state(s)) return st;
     if (grover_status st = check_marked(s, mk)) return st;
     if (k == 0) return GROVER_OK;
+    if (s->resident != 0) {
+        unsigned C = 0;
+        uint32_t nv = 0;
+        size_t smem = 0;
+        const bool exact_ok = s->acc == GROVER_ACC_DEFAULT || s->acc == GROVER_ACC_EXACT;
+        // automatic choice: where one cluster beats a grid-wide pass per
+        // iteration on GB300 (measured: the cluster's 16 SMs run out of FP64
+        // and integer throughput above these sizes)
+        const int auto_max = s->dtype == GROVER_C64 ? 17 : 15;
+        const bool wanted = s->resident == 1 || s->n <= auto_max;
+        if (wanted && exact_ok && resident_plan(s->n, s->dtype, &C, &nv, &smem)) {
+            ResArgs r;
+            r.amps = s->amps;
+            r.slice_vecs = nv;
+            r.mk = mk->dev;
+            r.k = k;
+            r.inv_n = ldexp(1.0, -s->n);
+            r.mu_out = s->sc.mu + s->mu_slot;
+            cudaError_t e = launch_resident(r, s->dtype, C, smem, s->stream);
+            if (e == cudaSuccess) {
+                s->mu_valid = true;
+                s->mu_key = mk->id;
+                return GROVER_OK;
+            }
+            (void)cudaGetLastError();
+            if (s->resident == 1) return cuda_fail(s, e, "persistent iterator launch");
+        } else if (s->resident == 1 && !(exact_ok && resident_plan(s->n, s->dtype, &C, &nv, &smem))) {
+            return fail(s, GROVER_EUNSUPPORTED, "the persistent iterator needs a state of at most 16 x 200 KiB and "
+                                                "GROVER_ACC_DEFAULT or GROVER_ACC_EXACT");
+        }
+    }
     if (grover_status st = ensure_mean(s, mk->dev, mk->id)) return st;
     for (uint64_t t = 0; t < k; ++t) {
         PassArgs a = pass_args(s, mk->dev);
@@ -395,8 +435,21 @@ grover_status grover_iterate(grover_state *s, const grover_marked *mk, uint64_t 
 grover_status grover_iterate_gate(grover_state *s, const grover_marked *mk, uint64_t k) {
     if (grover_status st = check_state(s)) return st;
     if (grover_status st = check_marked(s, mk)) return st;
-    (void)k;
-    return fail(s, GROVER_EUNSUPPORTED, "gate-level path not built");
+    if (k == 0) return GROVER_OK;
+    s->mu_valid = false;
+    const int ngroups = (s->n + 7) / 8;  // index bits [8g, 8g + 8)
+    for (uint64_t t = 0; t < k; ++t) {
+        CK(s, launch_oracle(s->amps, s->n, s->dtype, mk->dev, s->stream, s->geo), "oracle launch");
+        for (int pass = 0; pass < 2 * ngroups; ++pass) {
+            const int gi = pass % ngroups, lo = 8 * gi;
+            const int kb = s->n - lo < 8 ? s->n - lo : 8;
+            const bool first = pass < ngroups;  // first H^{(x)n}: scaled by 2^-n in total
+            const bool phase = pass == ngroups - 1;
+            CK(s, launch_wht_pass(s->amps, s->n, s->dtype, lo, kb, first, phase, s->stream, s->geo),
+               "Walsh-Hadamard pass launch");
+        }
+    }
+    return GROVER_OK;
 }
 
 grover_status grover_measure_probs(grover_state *s, double *out, int out_on_device) {

@@ -35,10 +35,18 @@ struct Cand {
     uint64_t idx;
 };
 
+// A complex mean as produced by one pass for the next: the mean itself, 2 mu,
+// and 2 mu as an unevaluated sum of two floats (hi, lo) per component.
+struct MeanSlot {
+    double2 mu;
+    double2 two;
+    float4 two32;  // (re hi, re lo, im hi, im lo)
+};
+
 // Device scratch owned by one state handle (one cudaMalloc, carved up).
 struct Scratch {
     double2 *partials;      // [kMaxGrid] per-CTA partial sums
-    double2 *mu;            // [2] double-buffered complex mean
+    MeanSlot *mu;           // [2] double-buffered complex mean
     unsigned *ticket;       // [1] last-CTA-done counter (always left at 0)
     int *status;            // [1] device status word (0 = ok)
     Cand *cand;             // [(kTopMGrid + 1) * kTopMMax] per-CTA top-m candidates + result
@@ -59,8 +67,8 @@ struct PassArgs {
     void *amps;
     uint64_t nvec;          // number of 16-byte vectors in the state
     MarkedDev mk;
-    const double2 *mu_in;   // mean used by this pass (device)
-    double2 *mu_out;        // mean produced for the next pass (device)
+    const MeanSlot *mu_in;  // mean used by this pass (device)
+    MeanSlot *mu_out;       // mean produced for the next pass (device)
     double2 *partials;
     unsigned *ticket;
     double inv_n;           // 1 / N
@@ -97,6 +105,28 @@ cudaError_t launch_norm_success(const void *amps, int n, grover_dtype dt, const 
 cudaError_t launch_topm(const void *amps, int n, grover_dtype dt, int m, Scratch &sc,
                         cudaStream_t st, const Geometry &g);
 
+// ---- persistent on-chip iterator (k_resident.cu) ---------------------------
+constexpr int kResMaxCluster = 16;          // CTAs per cluster (non-portable size)
+constexpr size_t kResSmemMax = 200 * 1024;  // dynamic shared memory per CTA
+struct ResArgs {
+    void *amps;
+    uint32_t slice_vecs;    // 16-byte vectors held by each CTA
+    MarkedDev mk;
+    uint64_t k;             // iterations
+    double inv_n;           // 1 / N
+    MeanSlot *mu_out;       // mean of O c after the last iteration
+};
+// false if the state does not fit one cluster's shared memory
+bool resident_plan(int n, grover_dtype dt, unsigned *C, uint32_t *slice_vecs, size_t *smem);
+cudaError_t launch_resident(const ResArgs &a, grover_dtype dt, unsigned C, size_t smem, cudaStream_t st);
+
+// ---- conventional circuit (k_gate.cu) ---------------------------------------
+// One Walsh-Hadamard pass over index bits [lo, lo + kb) (kb <= 8; lo = 0 or
+// lo >= 4), scaled by 2^-kb if `scaled`, negating every amplitude but index 0
+// if `negate` (the conditional phase shift 2|0><0| - I).
+cudaError_t launch_wht_pass(void *amps, int n, grover_dtype dt, int lo, int kb, bool scaled, bool negate,
+                            cudaStream_t st, const Geometry &g);
+
 // ---- errors (grover_api.cu) ------------------------------------------------
 // Sets the message grover_last_error(NULL) returns on this host thread.
 void set_thread_error(const char *msg);
@@ -114,6 +144,7 @@ struct grover_state {
     grv::Geometry geo;
     void *scratch_base;
     grv::Scratch sc;
+    int resident;           // -1 auto, 0 never, 1 required (grover_set_option)
     int mu_slot;            // which mu[] holds the current mean
     bool mu_valid;          // cached mean of flip_key(c) is valid
     uint64_t mu_key;        // 0: mean of c itself; else id of the marked set applied

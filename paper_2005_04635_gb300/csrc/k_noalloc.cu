@@ -27,7 +27,7 @@ namespace {
 
 constexpr int kNoAllocSlots = 2048;  // per-CTA partial sums: at most this many CTAs per pass
 constexpr size_t kPartialsBytes = sizeof(double2) * kNoAllocSlots;
-constexpr size_t kMuOffset = kPartialsBytes;           // double2 mu[2]
+constexpr size_t kMuOffset = kPartialsBytes;           // MeanSlot mu[2] (96 bytes)
 constexpr size_t kTicketOffset = kMuOffset + 256;      // unsigned ticket
 constexpr size_t kNoAllocBytes = kTicketOffset + 256;  // 33,280 bytes
 
@@ -114,7 +114,7 @@ extern "C" grover_status grover_iterate_noalloc(void *dev_amps, int n, grover_dt
     char *base = nullptr;
     if (grover_status st = scratch_address(dev, &base)) return st;
     double2 *partials = (double2 *)base;
-    double2 *mu = (double2 *)(base + kMuOffset);
+    MeanSlot *mu = (MeanSlot *)(base + kMuOffset);
     unsigned *ticket = (unsigned *)(base + kTicketOffset);
     cudaStream_t stream = (cudaStream_t)cuda_stream;
 

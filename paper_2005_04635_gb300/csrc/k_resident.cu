@@ -1,0 +1,311 @@
+// k_resident.cu -- persistent on-chip Grover iterator for small states.
+//
+// One thread-block cluster of C CTAs (C <= 16) runs all k iterations of the
+// proposed grover_search loop in one launch.  CTA r keeps amplitudes
+// [r*L, (r+1)*L) in its shared memory from the first load to the final store,
+// together with a bitmask of the marked indices of its slice (the oracle's
+// solution list, Algorithm "n-qubit Oracle").  Each iteration (Algorithm
+// "n-qubit Inversion about Mean"):
+//   1. every thread updates its amplitudes in shared memory,
+//        c <- 2 mu - O c,
+//      and adds O c_new into a 128-bit fixed-point sum (exact: 100 fractional
+//      bits; complex64 adds the FP32 pairwise sum of each 8-amplitude group);
+//   2. the CTA reduces its threads' sums exactly (integer shuffles) into a
+//      partial in its own shared memory;
+//   3. a hardware cluster barrier (release / acquire), then every CTA reads
+//      the C partials through distributed shared memory and adds them in
+//      integers, so all CTAs obtain the bitwise identical next mean without
+//      any global-memory round trip or spin-wait.
+// Partials are double buffered, so one barrier per iteration suffices: a CTA
+// can overwrite a slot only after every CTA has passed the next barrier, which
+// each CTA reaches only after it has read that slot.
+//
+// The fixed-point window is |x| < 16: for N <= 2^22 the whole state sums to
+// less than 2^26 in magnitude, so no 128-bit sum can overflow.  Larger
+// magnitudes, Inf and NaN go to an FP64 side sum combined in a fixed order.
+#include <cooperative_groups.h>
+
+#include "fixed_sum.cuh"
+#include "grover_internal.cuh"
+
+namespace grv {
+namespace {
+
+namespace cg = cooperative_groups;
+
+constexpr int kResThreads = 256;
+constexpr int kResWarps = kResThreads / 32;
+
+template <class T> struct Vec;
+template <> struct Vec<float> {
+    using V = float4;
+    static constexpr int APV = 2;
+};
+template <> struct Vec<double> {
+    using V = double2;
+    static constexpr int APV = 1;
+};
+
+__device__ __forceinline__ float flip(float x, uint32_t f) { return __uint_as_float(__float_as_uint(x) ^ (f << 31)); }
+__device__ __forceinline__ double flip(double x, uint32_t f) {
+    return __hiloint2double(__double2hiint(x) ^ (int)(f << 31), __double2loint(x));
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// mean = (integer sum * 2^-100 + side sum) / N, rounded once for the integer part
+__device__ __forceinline__ void write_mean_slot(MeanSlot *ms, u128 r, u128 i, double sr, double si, double inv_n) {
+    const double mr = (i192_to_double(i192_from(r)) * 0x1p-100 + sr) * inv_n;
+    const double mi = (i192_to_double(i192_from(i)) * 0x1p-100 + si) * inv_n;
+    const double tr = 2.0 * mr, ti = 2.0 * mi;
+    const float hr = (float)tr, hi = (float)ti;
+    ms->mu = make_double2(mr, mi);
+    ms->two = make_double2(tr, ti);
+    ms->two32 = make_float4(hr, (float)(tr - (double)hr), hi, (float)(ti - (double)hi));
+}
+
+template <int G, class T> __device__ __forceinline__ T pairwise(const T *v) {
+    if constexpr (G == 1) return v[0];
+    else if constexpr (G == 2) return v[0] + v[1];
+    else return pairwise<G / 2>(v) + pairwise<G / 2>(v + G / 2);
+}
+
+struct Part {
+    unsigned long long rl, rh, il, ih;
+    double sr, si;
+    int side;  // any side sum in this CTA
+};
+
+template <class T>
+__global__ void __launch_bounds__(kResThreads) k_resident_cluster(ResArgs a) {
+    using V = typename Vec<T>::V;
+    constexpr int APV = Vec<T>::APV;
+    constexpr int U = 4;  // vectors per thread per group
+    cg::cluster_group cl = cg::this_cluster();
+    const unsigned rank = cl.block_rank(), C = cl.num_blocks();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    extern __shared__ __align__(16) unsigned char smem[];
+    V *sl = reinterpret_cast<V *>(smem);
+    const uint32_t nv = a.slice_vecs;
+    const uint32_t nbits = nv * APV, nwords = (nbits + 31) / 32;
+    uint32_t *fm = reinterpret_cast<uint32_t *>(smem + (size_t)nv * sizeof(V));
+    __shared__ Part part[2];
+    __shared__ unsigned long long wint[kResWarps][4];
+    __shared__ double wside[kResWarps][2];
+    __shared__ MeanSlot s_mu;
+
+    V *g = static_cast<V *>(a.amps) + (size_t)rank * nv;
+    const uint64_t a0 = (uint64_t)rank * nbits;
+
+    for (uint32_t j = threadIdx.x; j < nv; j += kResThreads) sl[j] = g[j];
+    for (uint32_t w = threadIdx.x; w < nwords; w += kResThreads) fm[w] = 0u;
+    __syncthreads();
+    if (a.mk.mode == MARK_LIST) {
+        for (uint64_t i = threadIdx.x; i < a.mk.m; i += kResThreads) {
+            const uint64_t x = a.mk.list[i];
+            if (x >= a0 && x < a0 + nbits) atomicOr(fm + ((x - a0) >> 5), 1u << (uint32_t)((x - a0) & 31));
+        }
+    } else if (a.mk.mode == MARK_BITS) {
+        for (uint32_t e = threadIdx.x; e < nbits; e += kResThreads) {
+            const uint64_t x = a0 + e;
+            if ((a.mk.words[x >> 5] >> (uint32_t)(x & 31)) & 1u) atomicOr(fm + (e >> 5), 1u << (e & 31));
+        }
+    }
+    __syncthreads();
+
+    // t = -1 computes the first mean, t = 0..k-1 are the iterations
+    for (long long t = -1; t < (long long)a.k; ++t) {
+        const bool upd = t >= 0;
+        const int slot = (int)((t + 1) & 1);
+        T two_re = T(0), two_im = T(0), lo_re = T(0), lo_im = T(0);
+        if (upd) {
+            if constexpr (APV == 2) {
+                two_re = s_mu.two32.x;
+                lo_re = s_mu.two32.y;
+                two_im = s_mu.two32.z;
+                lo_im = s_mu.two32.w;
+            } else {
+                two_re = s_mu.two.x;
+                two_im = s_mu.two.y;
+            }
+        }
+        u128 ar = 0, ai = 0;
+        double sr = 0.0, si = 0.0;
+        for (uint32_t j0 = threadIdx.x; j0 < nv; j0 += U * kResThreads) {
+            T gr[U * APV], gi[U * APV];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const uint32_t j = j0 + u * kResThreads;
+                if (j >= nv) {
+#pragma unroll
+                    for (int q = 0; q < APV; ++q) gr[u * APV + q] = gi[u * APV + q] = T(0);
+                    continue;
+                }
+                V c = sl[j];
+                const uint32_t e = j * APV;
+                const uint32_t f = (fm[e >> 5] >> (e & 31)) & ((1u << APV) - 1u);
+                if constexpr (APV == 2) {
+                    const uint32_t f0 = f & 1u, f1 = f >> 1;
+                    if (upd) {
+                        c.x = (two_re - flip(c.x, f0)) + lo_re;
+                        c.y = (two_im - flip(c.y, f0)) + lo_im;
+                        c.z = (two_re - flip(c.z, f1)) + lo_re;
+                        c.w = (two_im - flip(c.w, f1)) + lo_im;
+                        sl[j] = c;
+                    }
+                    gr[2 * u] = flip(c.x, f0);
+                    gi[2 * u] = flip(c.y, f0);
+                    gr[2 * u + 1] = flip(c.z, f1);
+                    gi[2 * u + 1] = flip(c.w, f1);
+                } else {
+                    if (upd) {
+                        c.x = two_re - flip(c.x, f);
+                        c.y = two_im - flip(c.y, f);
+                        sl[j] = c;
+                    }
+                    gr[u] = flip(c.x, f);
+                    gi[u] = flip(c.y, f);
+                }
+            }
+            if constexpr (APV == 2) {
+                fix_add<4>(ar, sr, pairwise<U * APV>(gr));
+                fix_add<4>(ai, si, pairwise<U * APV>(gi));
+            } else {
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    fix_add<4>(ar, sr, gr[u]);
+                    fix_add<4>(ai, si, gi[u]);
+                }
+            }
+        }
+        // CTA partial: exact integer sums, side sums (if any) in a fixed tree order
+        ar = warp_sum_u128(ar);
+        ai = warp_sum_u128(ai);
+        const int any_side = __syncthreads_or(sr != 0.0 || si != 0.0);
+        if (any_side) {
+            sr = warp_sum(sr);
+            si = warp_sum(si);
+        }
+        if (lane == 0) {
+            wint[warp][0] = (unsigned long long)ar;
+            wint[warp][1] = (unsigned long long)(ar >> 64);
+            wint[warp][2] = (unsigned long long)ai;
+            wint[warp][3] = (unsigned long long)(ai >> 64);
+            wside[warp][0] = sr;
+            wside[warp][1] = si;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            u128 r = 0, i = 0;
+            double s1 = 0.0, s2 = 0.0;
+            if (lane < kResWarps) {
+                r = ((u128)wint[lane][1] << 64) | wint[lane][0];
+                i = ((u128)wint[lane][3] << 64) | wint[lane][2];
+                s1 = wside[lane][0];
+                s2 = wside[lane][1];
+            }
+            r = warp_sum_u128(r);
+            i = warp_sum_u128(i);
+            if (any_side) {
+                s1 = warp_sum(s1);
+                s2 = warp_sum(s2);
+            }
+            if (lane == 0) part[slot] = Part{(unsigned long long)r, (unsigned long long)(r >> 64),
+                                             (unsigned long long)i, (unsigned long long)(i >> 64), s1, s2, any_side};
+        }
+        cl.sync();
+        if (warp == 0) {
+            u128 r = 0, i = 0;
+            double s1 = 0.0, s2 = 0.0;
+            int side = 0;
+            if (lane < (int)C) {
+                const Part *rp = cl.map_shared_rank(&part[slot], lane);
+                r = ((u128)rp->rh << 64) | rp->rl;
+                i = ((u128)rp->ih << 64) | rp->il;
+                s1 = rp->sr;
+                s2 = rp->si;
+                side = rp->side;
+            }
+            r = warp_sum_u128(r);
+            i = warp_sum_u128(i);
+            if (__any_sync(0xffffffffu, side)) {
+                s1 = warp_sum(s1);
+                s2 = warp_sum(s2);
+            }
+            if (lane == 0) write_mean_slot(&s_mu, r, i, s1, s2, a.inv_n);
+        }
+        __syncthreads();
+    }
+    for (uint32_t j = threadIdx.x; j < nv; j += kResThreads) g[j] = sl[j];
+    if (rank == 0 && threadIdx.x == 0) *a.mu_out = s_mu;
+    cl.sync();  // keep every CTA's partial slots alive until all have read them
+}
+
+template <class T> cudaError_t launch_cluster_t(const ResArgs &a, unsigned C, size_t smem, cudaStream_t st) {
+    auto kern = k_resident_cluster<T>;
+    static size_t smem_set = 0;
+    cudaError_t e;
+    if (smem > smem_set) {
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+            return e;
+        smem_set = smem;
+    }
+    static bool nonportable = false;
+    if (C > 8 && !nonportable) {
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess) return e;
+        nonportable = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(kResThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    if ((e = cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg)) != cudaSuccess) return e;
+    if (clusters < 1) return cudaErrorNotSupported;
+    return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+}  // namespace
+
+// Chooses the cluster size: enough CTAs for the state to fit their shared
+// memory, and up to one 16-byte vector per thread to spread the arithmetic.
+bool resident_plan(int n, grover_dtype dt, unsigned *C_out, uint32_t *slice_vecs, size_t *smem_out) {
+    const uint64_t N = 1ull << n;
+    const int apv = dt == GROVER_C64 ? 2 : 1;
+    const uint64_t nvec = N / apv;
+    for (unsigned C = 1; C <= (unsigned)kResMaxCluster; C <<= 1) {
+        if (nvec % C) break;
+        const uint64_t nv = nvec / C;
+        const size_t smem = (size_t)nv * 16 + ((nv * apv + 31) / 32) * 4;
+        if (smem > kResSmemMax) continue;
+        // spread small states over more CTAs while each thread keeps >= 1 vector
+        unsigned Cw = C;
+        while (Cw < (unsigned)kResMaxCluster && nvec / (Cw * 2) >= (uint64_t)kResThreads && nvec % (Cw * 2) == 0) Cw <<= 1;
+        const uint64_t nvw = nvec / Cw;
+        *C_out = Cw;
+        *slice_vecs = (uint32_t)nvw;
+        *smem_out = (size_t)nvw * 16 + ((nvw * apv + 31) / 32) * 4;
+        return true;
+    }
+    return false;
+}
+
+cudaError_t launch_resident(const ResArgs &a, grover_dtype dt, unsigned C, size_t smem, cudaStream_t st) {
+    if (dt == GROVER_C64) return launch_cluster_t<float>(a, C, smem, st);
+    return launch_cluster_t<double>(a, C, smem, st);
+}
+
+}  // namespace grv

@@ -17,6 +17,7 @@
 // SMs.  The grid combine is a last-CTA-done ticket: the final CTA sums the
 // per-CTA partials in a fixed order, so the mean is bitwise reproducible and no
 // CTA ever waits on another.
+#include "fixed_sum.cuh"
 #include "grover_internal.cuh"
 
 #include <math.h>
@@ -116,7 +117,7 @@ template <int APV> __device__ __forceinline__ uint32_t mask_bits(const uint32_t 
 
 // ---- accumulators of the complex sum ------------------------------------------------
 // A thread sums the G = kUnroll * APV values of one tile ("load group") and
-// adds that to its running sum.  Pairwise summation of the group is exact when
+// adds that to its running sum.  Pairwise summation of a group is exact when
 // the values are equal, which they are for every unmarked amplitude of a
 // uniform-start search: no rounding bias repeats across the N/G groups.
 template <int G, class T> __device__ __forceinline__ T pairwise(const T *v) {
@@ -126,7 +127,12 @@ template <int G, class T> __device__ __forceinline__ T pairwise(const T *v) {
     else return pairwise<G / 2>(v) + pairwise<G / 2>(v + G / 2);
 }
 
-// complex128: FP64 pairwise group sum, FP64 running sum.
+// Internal accumulation mode of the complex64 default: FP32 pairwise group
+// sums, added exactly as fixed point above the group.
+constexpr int ACC_HYBRID = 16;
+
+// FP modes: running sums in S, block tree in S, per-CTA partial in FP64.
+// complex128, GROVER_ACC_FP64: FP64 pairwise group sum, FP64 running sum.
 struct AccD {
     double re = 0.0, im = 0.0;
     template <int G> __device__ __forceinline__ void add_group(const double *r, const double *i) {
@@ -171,87 +177,44 @@ struct AccKahan {
         }
     }
 };
-
-// GROVER_ACC_EXACT: magnitudes below 1 are added exactly as 128-bit integers
-// in units of 2^-100 (bits below 2^-100 are dropped: < 2^-100 per amplitude),
-// on the integer pipe; larger magnitudes, Inf and NaN go to an FP64 side sum.
-// A thread's integer sum stays below 2^115 for any 2^32 amplitudes.
-constexpr int kFixLsb = 100;
-__device__ __forceinline__ void fix_add(unsigned __int128 &acc, double &side, double x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const unsigned e = (unsigned)(b >> 52) & 0x7FFu;
-    if (e >= 1023u) {
-        side += x;
-        return;
-    }
-    const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | ((unsigned long long)(e != 0u) << 52);
-    const int sh = (int)e - (1075 - kFixLsb);  // x = m * 2^(sh - kFixLsb)
-    unsigned __int128 v;
-    if (sh >= 0) v = (unsigned __int128)m << sh;
-    else v = sh > -64 ? (unsigned __int128)(m >> (-sh)) : (unsigned __int128)0;
-    const unsigned __int128 neg = (unsigned __int128)(__int128)((long long)b >> 63);
-    acc += (v ^ neg) - neg;
-}
-__device__ __forceinline__ void fix_add(unsigned __int128 &acc, double &side, float x) {
-    const unsigned b = __float_as_uint(x);
-    const unsigned e = (b >> 23) & 0xFFu;
-    if (e >= 127u) {
-        side += (double)x;
-        return;
-    }
-    const unsigned long long m = (b & 0x7FFFFFu) | ((unsigned)(e != 0u) << 23);
-    const int sh = (int)e - (150 - kFixLsb);
-    unsigned __int128 v;
-    if (sh >= 0) v = (unsigned __int128)m << sh;
-    else v = sh > -24 ? (unsigned __int128)(m >> (-sh)) : (unsigned __int128)0;
-    const unsigned __int128 neg = (unsigned __int128)(__int128)((int)b >> 31);
-    acc += (v ^ neg) - neg;
-}
-struct AccX {
-    unsigned __int128 r = 0, i = 0;
-    double side_r = 0.0, side_i = 0.0;
-    template <int G, class T> __device__ __forceinline__ void add_group(const T *re, const T *im) {
-#pragma unroll
-        for (int j = 0; j < G; ++j) {
-            fix_add(r, side_r, re[j]);
-            fix_add(i, side_i, im[j]);
-        }
-    }
-};
-
-// double-double arithmetic for combining exact per-thread sums (plain adds only)
-struct DD {
-    double h, l;
-};
-__device__ __forceinline__ DD dd_add(DD a, DD b) {
-    const double s = __dadd_rn(a.h, b.h);
-    const double bb = __dsub_rn(s, a.h);
-    double e = __dadd_rn(__dsub_rn(a.h, __dsub_rn(s, bb)), __dsub_rn(b.h, bb));
-    e = __dadd_rn(e, __dadd_rn(a.l, b.l));
-    const double h = __dadd_rn(s, e);
-    return DD{h, __dsub_rn(e, __dsub_rn(h, s))};
-}
-__device__ __forceinline__ DD dd_from_fix(unsigned __int128 u, double side) {
-    const __int128 x = (__int128)u;
-    const double h = (double)x;
-    const double l = (double)(x - (__int128)h);
-    return dd_add(DD{h * 0x1p-100, l * 0x1p-100}, DD{side, 0.0});
-}
-
-template <class T, int ACC> struct AccSel;
-template <int ACC> struct AccSel<double, ACC> { using A = AccD; using S = double; };
-template <> struct AccSel<double, GROVER_ACC_EXACT> { using A = AccX; using S = double; };
-template <> struct AccSel<float, GROVER_ACC_EXACT> { using A = AccX; using S = double; };
-template <> struct AccSel<float, GROVER_ACC_FP64> { using A = AccF64; using S = double; };
-template <> struct AccSel<float, GROVER_ACC_FP32> { using A = AccF32; using S = float; };
-template <> struct AccSel<float, GROVER_ACC_KAHAN> { using A = AccKahan; using S = float; };
-
 __device__ __forceinline__ double2 acc_value(const AccD &a) { return make_double2(a.re, a.im); }
 __device__ __forceinline__ double2 acc_value(const AccF64 &a) { return make_double2(a.re, a.im); }
 __device__ __forceinline__ float2 acc_value(const AccF32 &a) { return make_float2(a.re, a.im); }
 __device__ __forceinline__ float2 acc_value(const AccKahan &a) {
     return make_float2(__fadd_rn(a.sr, a.cr), __fadd_rn(a.si, a.ci));
 }
+
+// Integer modes (fixed_sum.cuh).  Window exponents keep every 128-bit CTA
+// partial in range: per element |x| < 1 (GROVER_ACC_EXACT), per 8-value FP32
+// group |x| < 16 (ACC_HYBRID).
+struct AccX {  // GROVER_ACC_EXACT: every amplitude exactly
+    u128 r = 0, i = 0;
+    double side_r = 0.0, side_i = 0.0;
+    template <int G, class T> __device__ __forceinline__ void add_group(const T *re, const T *im) {
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            fix_add<0>(r, side_r, re[j]);
+            fix_add<0>(i, side_i, im[j]);
+        }
+    }
+};
+struct AccH {  // ACC_HYBRID: FP32 pairwise group, exact above
+    u128 r = 0, i = 0;
+    double side_r = 0.0, side_i = 0.0;
+    template <int G> __device__ __forceinline__ void add_group(const float *re, const float *im) {
+        fix_add<4>(r, side_r, pairwise<G>(re));
+        fix_add<4>(i, side_i, pairwise<G>(im));
+    }
+};
+
+template <class T, int ACC> struct AccSel;
+template <int ACC> struct AccSel<double, ACC> { using A = AccD; using S = double; static constexpr bool INT = false; };
+template <> struct AccSel<double, GROVER_ACC_EXACT> { using A = AccX; using S = double; static constexpr bool INT = true; };
+template <> struct AccSel<float, GROVER_ACC_EXACT> { using A = AccX; using S = double; static constexpr bool INT = true; };
+template <> struct AccSel<float, ACC_HYBRID> { using A = AccH; using S = double; static constexpr bool INT = true; };
+template <> struct AccSel<float, GROVER_ACC_FP64> { using A = AccF64; using S = double; static constexpr bool INT = false; };
+template <> struct AccSel<float, GROVER_ACC_FP32> { using A = AccF32; using S = float; static constexpr bool INT = false; };
+template <> struct AccSel<float, GROVER_ACC_KAHAN> { using A = AccKahan; using S = float; static constexpr bool INT = false; };
 
 // ---- deterministic block reduction (result valid in thread 0) -----------------------
 template <class S> __device__ __forceinline__ S warp_sum(S v) {
@@ -273,7 +236,18 @@ template <class S> __device__ __forceinline__ S block_sum(S v, S *sm) {
     return v;
 }
 
-// Per-CTA partial -> partials[], last CTA combines in FP64 in a fixed order.
+// The producer of a mean also stores what the consumers need, so that no
+// consuming thread spends FP64 instructions on it.
+__device__ __forceinline__ void write_mean(MeanSlot *ms, double mr, double mi) {
+    const double tr = 2.0 * mr, ti = 2.0 * mi;
+    const float hr = (float)tr, hi = (float)ti;
+    ms->mu = make_double2(mr, mi);
+    ms->two = make_double2(tr, ti);
+    ms->two32 = make_float4(hr, (float)(tr - (double)hr), hi, (float)(ti - (double)hi));
+}
+
+// FP modes: per-CTA partial -> partials[], last CTA combines in FP64 in a
+// fixed order.
 __device__ __forceinline__ void grid_combine(double2 part, const PassArgs &a) {
     __shared__ double sm[kThreads / 32];
     __shared__ unsigned s_last;
@@ -295,55 +269,115 @@ __device__ __forceinline__ void grid_combine(double2 part, const PassArgs &a) {
     sr = block_sum(sr, sm);
     si = block_sum(si, sm);
     if (threadIdx.x == 0) {
-        *a.mu_out = make_double2(sr * a.inv_n, si * a.inv_n);
+        write_mean(a.mu_out, sr * a.inv_n, si * a.inv_n);
         *a.ticket = 0u;
     }
 }
 
-__device__ __forceinline__ DD warp_dd(DD v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-        v = dd_add(v, DD{__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)});
-    return v;
-}
-__device__ __forceinline__ DD block_dd(DD v, DD *sm) {
+// Integer modes: the CTA's exact partial (two 128-bit integers) and its FP64
+// side sums go to partials[3b .. 3b+2]; the last CTA adds the integers in 192
+// bits (exact, any order) and the side sums in a fixed order, and rounds once.
+__device__ __forceinline__ void int_combine(u128 r, u128 i, double sr, double si, const PassArgs &a) {
+    __shared__ unsigned long long wi[kThreads / 32][6];
+    __shared__ double wsd[kThreads / 32][2];
+    __shared__ unsigned s_last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    v = warp_dd(v);
-    __syncthreads();
-    if (lane == 0) sm[warp] = v;
+    // CTA partial (thread 0)
+    r = warp_sum_u128(r);
+    i = warp_sum_u128(i);
+    const int any_side = __syncthreads_or(sr != 0.0 || si != 0.0);
+    if (any_side) {
+        sr = warp_sum(sr);
+        si = warp_sum(si);
+    }
+    if (lane == 0) {
+        wi[warp][0] = (unsigned long long)r;
+        wi[warp][1] = (unsigned long long)(r >> 64);
+        wi[warp][2] = (unsigned long long)i;
+        wi[warp][3] = (unsigned long long)(i >> 64);
+        wsd[warp][0] = sr;
+        wsd[warp][1] = si;
+    }
     __syncthreads();
     if (warp == 0) {
-        v = (lane < kThreads / 32) ? sm[lane] : DD{0.0, 0.0};
-        v = warp_dd(v);
-    }
-    return v;
-}
-// Exact mode: per-CTA double-double partials in partials[2b], partials[2b+1];
-// the last CTA adds them in a fixed order in double-double.
-__device__ __forceinline__ void grid_combine_dd(DD re, DD im, const PassArgs &a) {
-    __shared__ DD sm[kThreads / 32];
-    __shared__ unsigned s_last;
-    if (threadIdx.x == 0) {
-        a.partials[2 * blockIdx.x] = make_double2(re.h, re.l);
-        a.partials[2 * blockIdx.x + 1] = make_double2(im.h, im.l);
-        __threadfence();
-        unsigned t = atomicAdd(a.ticket, 1u);
-        s_last = (t == gridDim.x - 1) ? 1u : 0u;
+        u128 br = 0, bi = 0;
+        double bsr = 0.0, bsi = 0.0;
+        if (lane < kThreads / 32) {
+            br = ((u128)wi[lane][1] << 64) | wi[lane][0];
+            bi = ((u128)wi[lane][3] << 64) | wi[lane][2];
+            bsr = wsd[lane][0];
+            bsi = wsd[lane][1];
+        }
+        br = warp_sum_u128(br);
+        bi = warp_sum_u128(bi);
+        if (any_side) {
+            bsr = warp_sum(bsr);
+            bsi = warp_sum(bsi);
+        }
+        if (lane == 0) {
+            double2 *p = a.partials + 3 * blockIdx.x;
+            p[0] = make_double2(__longlong_as_double((long long)(unsigned long long)br),
+                                __longlong_as_double((long long)(unsigned long long)(br >> 64)));
+            p[1] = make_double2(__longlong_as_double((long long)(unsigned long long)bi),
+                                __longlong_as_double((long long)(unsigned long long)(bi >> 64)));
+            p[2] = make_double2(bsr, bsi);
+            __threadfence();
+            s_last = (atomicAdd(a.ticket, 1u) == gridDim.x - 1) ? 1u : 0u;
+        }
     }
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    DD sr{0.0, 0.0}, si{0.0, 0.0};
+    I192 tr{0, 0, 0}, ti{0, 0, 0};
+    double ssr = 0.0, ssi = 0.0;
     for (unsigned j = threadIdx.x; j < gridDim.x; j += kThreads) {
-        const double2 qr = __ldcg(a.partials + 2 * j), qi = __ldcg(a.partials + 2 * j + 1);
-        sr = dd_add(sr, DD{qr.x, qr.y});
-        si = dd_add(si, DD{qi.x, qi.y});
+        const double2 q0 = __ldcg(a.partials + 3 * j), q1 = __ldcg(a.partials + 3 * j + 1),
+                      q2 = __ldcg(a.partials + 3 * j + 2);
+        i192_add(tr, i192_from(((u128)(unsigned long long)__double_as_longlong(q0.y) << 64) |
+                               (unsigned long long)__double_as_longlong(q0.x)));
+        i192_add(ti, i192_from(((u128)(unsigned long long)__double_as_longlong(q1.y) << 64) |
+                               (unsigned long long)__double_as_longlong(q1.x)));
+        ssr += q2.x;
+        ssi += q2.y;
     }
-    sr = block_dd(sr, sm);
-    si = block_dd(si, sm);
-    if (threadIdx.x == 0) {
-        *a.mu_out = make_double2(__dadd_rn(sr.h, sr.l) * a.inv_n, __dadd_rn(si.h, si.l) * a.inv_n);
-        *a.ticket = 0u;
+    const int any = __syncthreads_or(ssr != 0.0 || ssi != 0.0);
+    tr = warp_sum_i192(tr);
+    ti = warp_sum_i192(ti);
+    if (any) {
+        ssr = warp_sum(ssr);
+        ssi = warp_sum(ssi);
+    }
+    if (lane == 0) {
+        wi[warp][0] = tr.w0;
+        wi[warp][1] = tr.w1;
+        wi[warp][2] = tr.w2;
+        wi[warp][3] = ti.w0;
+        wi[warp][4] = ti.w1;
+        wi[warp][5] = ti.w2;
+        wsd[warp][0] = ssr;
+        wsd[warp][1] = ssi;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        I192 xr{0, 0, 0}, xi{0, 0, 0};
+        double yr = 0.0, yi = 0.0;
+        if (lane < kThreads / 32) {
+            xr = I192{wi[lane][0], wi[lane][1], wi[lane][2]};
+            xi = I192{wi[lane][3], wi[lane][4], wi[lane][5]};
+            yr = wsd[lane][0];
+            yi = wsd[lane][1];
+        }
+        xr = warp_sum_i192(xr);
+        xi = warp_sum_i192(xi);
+        if (any) {
+            yr = warp_sum(yr);
+            yi = warp_sum(yi);
+        }
+        if (lane == 0) {
+            const double sum_r = i192_to_double(xr) * 0x1p-100, sum_i = i192_to_double(xi) * 0x1p-100;
+            write_mean(a.mu_out, (sum_r + yr) * a.inv_n, (sum_i + yi) * a.inv_n);
+            *a.ticket = 0u;
+        }
     }
 }
 
@@ -371,11 +405,17 @@ __global__ void __launch_bounds__(kThreads) k_pass(PassArgs a) {
     // two floats, so the update is not shifted by one shared rounding of 2 mu.
     T two_re = T(0), two_im = T(0), lo_re = T(0), lo_im = T(0);
     if (UPDATE) {
-        const double2 mu = *a.mu_in;
-        two_re = (T)(2.0 * mu.x);
-        two_im = (T)(2.0 * mu.y);
-        lo_re = (T)(2.0 * mu.x - (double)two_re);
-        lo_im = (T)(2.0 * mu.y - (double)two_im);
+        if constexpr (APV == 2) {
+            const float4 h = a.mu_in->two32;
+            two_re = h.x;
+            lo_re = h.y;
+            two_im = h.z;
+            lo_im = h.w;
+        } else {
+            const double2 t2 = a.mu_in->two;
+            two_re = t2.x;
+            two_im = t2.y;
+        }
     }
     auto upd = [&](T x, T two, T lo) -> T {
         if constexpr (APV == 2) return (two - x) + lo;
@@ -441,11 +481,8 @@ __global__ void __launch_bounds__(kThreads) k_pass(PassArgs a) {
         acc.template add_group<G>(gr, gi);
     }
 
-    if constexpr (ACC == GROVER_ACC_EXACT) {
-        __shared__ DD smd[kThreads / 32];
-        const DD r = block_dd(dd_from_fix(acc.r, acc.side_r), smd);
-        const DD im = block_dd(dd_from_fix(acc.i, acc.side_i), smd);
-        grid_combine_dd(r, im, a);
+    if constexpr (AccSel<T, ACC>::INT) {
+        int_combine(acc.r, acc.i, acc.side_r, acc.side_i, a);
     } else {
         // block tree in S precision, then FP64 partial
         __shared__ S sm[kThreads / 32];
@@ -587,7 +624,8 @@ cudaError_t dispatch(const PassArgs &a, grover_dtype dt, grover_accum acc, cudaS
     case GROVER_ACC_FP32: return dispatch_mark<float, GROVER_ACC_FP32, UPDATE>(a, st, g);
     case GROVER_ACC_KAHAN: return dispatch_mark<float, GROVER_ACC_KAHAN, UPDATE>(a, st, g);
     case GROVER_ACC_EXACT: return dispatch_mark<float, GROVER_ACC_EXACT, UPDATE>(a, st, g);
-    default: return dispatch_mark<float, GROVER_ACC_FP64, UPDATE>(a, st, g);
+    case GROVER_ACC_FP64: return dispatch_mark<float, GROVER_ACC_FP64, UPDATE>(a, st, g);
+    default: return dispatch_mark<float, ACC_HYBRID, UPDATE>(a, st, g);
     }
 }
 

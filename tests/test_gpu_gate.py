@@ -1,0 +1,111 @@
+"""The conventional circuit (grover_iterate_gate) against the oracle.
+
+Error bound: each butterfly stage of a Walsh-Hadamard pass rounds every output
+once, adding an error vector of norm <= u * ||state|| (the normalised stage is
+orthogonal; power-of-two scaling is exact), and an iteration has 2n stages, so
+after k iterations |error| <= 2 n k u (u = 2^-24 for complex64, 2^-53 for
+complex128), on top of the oracle's own rounding.
+"""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2005_04635_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "three_qubit_101.txt")
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2005_04635_gb300 import binding
+    binding.lib()
+    return binding
+
+
+def to_np(st):
+    torch.cuda.synchronize()
+    return st.amps.cpu().numpy().astype(np.complex128)
+
+
+def tol(dtype, n, k):
+    u = 2.0 ** -24 if dtype == "c64" else 2.0 ** -53
+    return 2 * n * max(k, 1) * u + (1e-13 if dtype == "c128" else 1e-7)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("n,m,k", [(1, 1, 1), (2, 1, 1), (3, 1, 2), (5, 2, 3), (8, 3, 5), (9, 1, 4), (12, 4, 6),
+                                   (16, 1, 3), (17, 2, 2), (20, 1, 2)])
+def test_gate_matches_oracle_circuit(B, dtype, n, m, k):
+    marked = inputs.marked_indices(n, m, seed=500 + n)
+    psi0 = inputs.gaussian_state(n, seed=501 + n)
+    if dtype == "c64":
+        psi0 = psi0.astype(np.complex64).astype(np.complex128)
+    st = B.State(n, dtype)
+    st.init_state(psi0)
+    st.iterate_gate(B.Marked(n, marked), k)
+    got = to_np(st)
+    ref = oracle.grover_gate(psi0.copy(), n, marked, k)
+    assert np.max(np.abs(got - ref)) <= tol(dtype, n, k)
+    # the circuit and the equivalent operator agree (no global phase)
+    ref_op = oracle.grover_operator(psi0.copy(), n, marked, k)
+    assert np.max(np.abs(got - ref_op)) <= tol(dtype, n, k) + 1e-12
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_gate_equals_operator_path_uniform(B, dtype):
+    n, m = 14, 3
+    marked = inputs.marked_indices(n, m, seed=77)
+    k = B.grover_optimal_iterations(n, m)
+    mk = B.Marked(n, marked)
+    a = B.State(n, dtype)
+    a.init_uniform()
+    a.iterate_gate(mk, k)
+    b = B.State(n, dtype)
+    b.init_uniform()
+    b.iterate(mk, k)
+    ga, gb = to_np(a), to_np(b)
+    c64_op = (k + 1) * 2.0 ** -22
+    assert np.max(np.abs(ga - gb)) <= tol(dtype, n, k) + (c64_op if dtype == "c64" else 1e-11)
+    ps_a, _ = a.success_prob(mk)
+    ref = oracle.grover_operator(oracle.init_uniform(n), n, marked, k)
+    assert abs(ps_a - oracle.success_prob(ref, n, marked)) <= (1e-10 if dtype == "c128" else 1e-4)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_gate_three_qubit_worked_example(B, dtype):
+    """The paper's measurement outcome (|101>, 94.531 % / 0.781 %) through the circuit."""
+    rows = []
+    for line in open(GOLDEN):
+        line = line.split("#", 1)[0].strip()
+        if line and line.split()[0] not in ("n", "marked", "iterations"):
+            a, b_ = line.split()
+            rows.append((int(a, 2), float(b_)))
+    st = B.State(3, dtype)
+    st.init_uniform()
+    st.iterate_gate(B.Marked(3, [5]), 2)
+    p = st.measure_probs()
+    for x, pct in rows:
+        assert round(100 * p[x], 3) == pytest.approx(pct, abs=1e-9)
+    idx, pp = st.measure_topm(1)
+    assert int(idx[0]) == 5
+
+
+def test_gate_bitmask_and_empty(B):
+    n = 10
+    marked = inputs.marked_indices(n, 300, seed=3)
+    psi0 = inputs.gaussian_state(n, seed=4)
+    for mk, mlist in ((B.Marked(n, bitmask=inputs.bitmask(n, marked)), marked), (B.Marked(n, []), [])):
+        st = B.State(n, "c128")
+        st.init_state(psi0)
+        st.iterate_gate(mk, 3)
+        ref = oracle.grover_gate(psi0.copy(), n, mlist, 3)
+        assert np.max(np.abs(to_np(st) - ref)) <= tol("c128", n, 3)

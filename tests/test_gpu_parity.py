@@ -50,13 +50,18 @@ def check_groups(psi, marked):
             assert np.all(grp == grp[0]), "amplitudes of one group differ bitwise"
 
 
+PATHS = {"auto": -1, "pass": 0}
+
+
+@pytest.mark.parametrize("path", ["auto", "pass"])
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
-@pytest.mark.parametrize("n,m", [(1, 1), (2, 1), (3, 1), (5, 2), (6, 1), (9, 3), (12, 1), (12, 4), (16, 16), (17, 1), (20, 1)])
-def test_uniform_full_run(B, dtype, n, m):
+@pytest.mark.parametrize("n,m", [(1, 1), (2, 1), (3, 1), (5, 2), (6, 1), (9, 3), (12, 1), (12, 4), (16, 16), (17, 1), (18, 2), (20, 1)])
+def test_uniform_full_run(B, dtype, n, m, path):
     marked = inputs.marked_indices(n, m, seed=n * 100 + m)
     k = B.grover_optimal_iterations(n, m)
     mk = B.Marked(n, marked)
     st = B.State(n, dtype)
+    st.set_resident(PATHS[path])
     st.init_uniform()
     st.iterate(mk, k)
     ps, nrm = st.success_prob(mk)
@@ -77,15 +82,17 @@ def test_uniform_full_run(B, dtype, n, m):
         assert sorted(idx.tolist()) == marked.tolist()
 
 
+@pytest.mark.parametrize("path", ["auto", "pass"])
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 @pytest.mark.parametrize("n,m,k", [(4, 3, 7), (10, 8, 60), (14, 8, 200), (15, 5, 31)])
-def test_gaussian_init(B, dtype, n, m, k):
+def test_gaussian_init(B, dtype, n, m, k, path):
     marked = inputs.marked_indices(n, m, seed=7 * n)
     psi0 = inputs.gaussian_state(n, seed=11 * n)
     if dtype == "c64":
         psi0 = psi0.astype(np.complex64).astype(np.complex128)  # the oracle starts from the stored values
     mk = B.Marked(n, marked)
     st = B.State(n, dtype)
+    st.set_resident(PATHS[path])
     st.init_state(psi0)
     st.iterate(mk, k)
     st.sync()
@@ -282,3 +289,58 @@ def test_invalid_marked_for_state(B):
         st.iterate(B.Marked(7, [1]), 1)
     with pytest.raises(B.GroverError):
         st.measure_topm(17)
+
+
+# ---- persistent on-chip iterator ----------------------------------------------------
+@pytest.mark.parametrize("dtype,n", [("c64", 1), ("c64", 3), ("c64", 11), ("c64", 18), ("c128", 1), ("c128", 2),
+                                     ("c128", 12), ("c128", 17)])
+def test_resident_forced(B, dtype, n):
+    """The persistent iterator (forced on) against the oracle, Gaussian start,
+    marked list and bitmask, then continued by the pass path (the mean it leaves
+    behind must be the mean of O c)."""
+    m = min(5, 1 << n)
+    marked = inputs.marked_indices(n, m, seed=70 + n)
+    psi0 = inputs.gaussian_state(n, seed=71 + n)
+    if dtype == "c64":
+        psi0 = psi0.astype(np.complex64).astype(np.complex128)
+    k1, k2 = 23, 9
+    ref1 = oracle.grover_operator(psi0.copy(), n, marked, k1)
+    ref2 = oracle.grover_operator(ref1.copy(), n, marked, k2)
+    tol = (lambda k: 1e-12) if dtype == "c128" else c64_tol
+    for mk in (B.Marked(n, marked), B.Marked(n, bitmask=inputs.bitmask(n, marked))):
+        st = B.State(n, dtype)
+        st.set_resident(1)
+        st.init_state(psi0)
+        st.iterate(mk, k1)
+        assert np.max(np.abs(to_np(st) - ref1)) <= tol(k1)
+        st.set_resident(0)
+        st.iterate(mk, k2)
+        assert np.max(np.abs(to_np(st) - ref2)) <= tol(k1 + k2)
+
+
+def test_resident_refuses_large_states(B):
+    st = B.State(19, "c64")
+    st.set_resident(1)
+    st.init_uniform()
+    with pytest.raises(B.GroverError) as ei:
+        st.iterate(B.Marked(19, [3]), 2)
+    assert ei.value.status == 8  # GROVER_EUNSUPPORTED
+    st2 = B.State(10, "c64")
+    st2.set_resident(1)
+    st2.set_accum("kahan")
+    with pytest.raises(B.GroverError):
+        st2.iterate(B.Marked(10, [3]), 2)
+
+
+def test_resident_deterministic_and_equal_groups(B):
+    n = 16
+    marked = inputs.marked_indices(n, 3, seed=90)
+    outs = []
+    for _ in range(2):
+        st = B.State(n, "c128")
+        st.set_resident(1)
+        st.init_uniform()
+        st.iterate(B.Marked(n, marked), B.grover_optimal_iterations(n, 3))
+        outs.append(to_np(st))
+    assert np.array_equal(outs[0], outs[1])
+    check_groups(outs[0], marked)

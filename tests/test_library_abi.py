@@ -101,6 +101,10 @@ def test_create_validation(lib):
     assert h.value is None
 
 
+def test_set_option_validation(lib):
+    assert lib.grover_set_option(None, 0, -1) == 1
+
+
 def test_null_handles(lib):
     for fn in ("grover_init_uniform", "grover_diffuse", "grover_sync"):
         assert getattr(lib, fn)(None) == 1
