@@ -115,7 +115,12 @@ typedef enum {
      *    0: always one fused pass per iteration;
      *    1: the persistent iterator wherever it can run (grover_iterate returns
      *       GROVER_EUNSUPPORTED where it cannot). */
-    GROVER_OPT_RESIDENT = 0
+    GROVER_OPT_RESIDENT = 0,
+    /* Engine of grover_iterate_gate's Walsh-Hadamard passes: -1 (default) the
+     * tensor cores for complex64 states with n >= 13, CUDA cores otherwise;
+     * 0 always CUDA cores; 1 the tensor cores (GROVER_EUNSUPPORTED for
+     * complex128 or n < 13). */
+    GROVER_OPT_GATE_ENGINE = 1
 } grover_option;
 
 /* Sets an execution option of the handle (see grover_option).  GROVER_EINVAL
@@ -176,12 +181,15 @@ grover_status grover_iterate(grover_state *s, const grover_marked *mk, uint64_t 
 
 /* k iterations of the conventional circuit (section "Background",
  * conventional grover_search): oracle, H^{(x)n}, 2|0><0| - I, H^{(x)n}.
- * H^{(x)n} is a product of Walsh-Hadamard transforms on groups of up to 8
- * index bits, one read + write pass over the state per group, with +-1
- * butterflies and exact power-of-two scaling (2^-n per iteration in total);
- * the phase shift is fused into the last pass of the first transform.  The
- * result equals grover_iterate's up to rounding (no global phase).  Invalidates
- * the cached mean. */
+ * H^{(x)n} is a product of Walsh-Hadamard transforms on groups of index bits,
+ * one read + write pass over the state per group, with exact power-of-two
+ * scaling (2^-n per iteration in total); the phase shift is fused into the
+ * last pass of the first transform.  Engines (GROVER_OPT_GATE_ENGINE): the
+ * tensor cores (complex64: 7-bit groups as dense +-1 matrix products,
+ * operands split into three bf16 slices, FP32 accumulation) or CUDA cores
+ * (8-bit groups, +-1 butterflies).  The result equals grover_iterate's up to
+ * rounding (no global phase).  Invalidates the cached mean; a tensor-core wait
+ * that gives up is reported by grover_sync (GROVER_ETIMEOUT). */
 grover_status grover_iterate_gate(grover_state *s, const grover_marked *mk, uint64_t k);
 
 /* floor(pi/4 * sqrt(2^n / m)), the iteration count that maximises the success

@@ -153,6 +153,10 @@ class State:
         """-1 automatic, 0 one pass per iteration, 1 the persistent on-chip iterator."""
         _check(lib().grover_set_option(self.handle, 0, int(value)), self.handle)
 
+    def set_gate_engine(self, value: int):
+        """-1 automatic, 0 CUDA-core butterflies, 1 tensor cores (complex64, n >= 13)."""
+        _check(lib().grover_set_option(self.handle, 1, int(value)), self.handle)
+
     def init_uniform(self):
         _check(lib().grover_init_uniform(self.handle), self.handle)
 

@@ -197,6 +197,7 @@ grover_status grover_create(grover_state **out, int n, grover_dtype dtype, void 
     s->sc.red = (double2 *)(base + L.red);
     s->sc.probs_tmp = nullptr;
     s->resident = -1;
+    s->gate_engine = -1;
     s->mu_slot = 0;
     s->mu_valid = false;
     s->mu_key = 0;
@@ -229,9 +230,11 @@ grover_status grover_set_accum(grover_state *s, grover_accum mode) {
 
 grover_status grover_set_option(grover_state *s, grover_option opt, int64_t value) {
     if (grover_status st = check_state(s)) return st;
-    if (opt != GROVER_OPT_RESIDENT) return fail(s, GROVER_EINVAL, "unknown option %d", (int)opt);
-    if (value < -1 || value > 1) return fail(s, GROVER_EINVAL, "GROVER_OPT_RESIDENT takes -1, 0 or 1");
-    s->resident = (int)value;
+    if (opt != GROVER_OPT_RESIDENT && opt != GROVER_OPT_GATE_ENGINE)
+        return fail(s, GROVER_EINVAL, "unknown option %d", (int)opt);
+    if (value < -1 || value > 1) return fail(s, GROVER_EINVAL, "option %d takes -1, 0 or 1", (int)opt);
+    if (opt == GROVER_OPT_RESIDENT) s->resident = (int)value;
+    else s->gate_engine = (int)value;
     return GROVER_OK;
 }
 
@@ -436,17 +439,29 @@ grover_status grover_iterate_gate(grover_state *s, const grover_marked *mk, uint
     if (grover_status st = check_state(s)) return st;
     if (grover_status st = check_marked(s, mk)) return st;
     if (k == 0) return GROVER_OK;
+    // tensor cores: complex64, 7-bit groups from bit 0 (needs n >= 13);
+    // CUDA cores: 8-bit groups, or a group the tensor-core pass does not cover
+    const bool tc_possible = s->dtype == GROVER_C64 && s->n >= 13;
+    if (s->gate_engine == 1 && !tc_possible)
+        return fail(s, GROVER_EUNSUPPORTED, "the tensor-core gate path needs a complex64 state with n >= 13");
+    const bool tc = tc_possible && s->gate_engine != 0;
+    const int gbits = tc ? 7 : 8;
+    const int ngroups = (s->n + gbits - 1) / gbits;
     s->mu_valid = false;
-    const int ngroups = (s->n + 7) / 8;  // index bits [8g, 8g + 8)
     for (uint64_t t = 0; t < k; ++t) {
         CK(s, launch_oracle(s->amps, s->n, s->dtype, mk->dev, s->stream, s->geo), "oracle launch");
         for (int pass = 0; pass < 2 * ngroups; ++pass) {
-            const int gi = pass % ngroups, lo = 8 * gi;
-            const int kb = s->n - lo < 8 ? s->n - lo : 8;
+            const int gi = pass % ngroups, lo = gbits * gi;
+            const int kb = s->n - lo < gbits ? s->n - lo : gbits;
             const bool first = pass < ngroups;  // first H^{(x)n}: scaled by 2^-n in total
             const bool phase = pass == ngroups - 1;
-            CK(s, launch_wht_pass(s->amps, s->n, s->dtype, lo, kb, first, phase, s->stream, s->geo),
-               "Walsh-Hadamard pass launch");
+            if (tc && tc_pass_supported(s->n, lo, kb)) {
+                CK(s, launch_wht_tc_pass(s->amps, s->n, lo, kb, first, phase, s->sc.status, s->stream, s->geo),
+                   "tensor-core Walsh-Hadamard pass launch");
+            } else {
+                CK(s, launch_wht_pass(s->amps, s->n, s->dtype, lo, kb, first, phase, s->stream, s->geo),
+                   "Walsh-Hadamard pass launch");
+            }
         }
     }
     return GROVER_OK;

@@ -127,6 +127,13 @@ cudaError_t launch_resident(const ResArgs &a, grover_dtype dt, unsigned C, size_
 cudaError_t launch_wht_pass(void *amps, int n, grover_dtype dt, int lo, int kb, bool scaled, bool negate,
                             cudaStream_t st, const Geometry &g);
 
+// ---- conventional circuit on tensor cores (k_gate_tc.cu), complex64 ---------
+// true if a tensor-core pass exists for bits [lo, lo + kb) of an n-qubit state
+bool tc_pass_supported(int n, int lo, int kb);
+// Walsh-Hadamard pass on the tensor cores; a wait that gives up sets *status = 2
+cudaError_t launch_wht_tc_pass(void *amps, int n, int lo, int kb, bool scaled, bool negate, int *status,
+                               cudaStream_t st, const Geometry &g);
+
 // ---- errors (grover_api.cu) ------------------------------------------------
 // Sets the message grover_last_error(NULL) returns on this host thread.
 void set_thread_error(const char *msg);
@@ -145,6 +152,7 @@ struct grover_state {
     void *scratch_base;
     grv::Scratch sc;
     int resident;           // -1 auto, 0 never, 1 required (grover_set_option)
+    int gate_engine;        // -1 auto, 0 CUDA cores, 1 tensor cores (grover_set_option)
     int mu_slot;            // which mu[] holds the current mean
     bool mu_valid;          // cached mean of flip_key(c) is valid
     uint64_t mu_key;        // 0: mean of c itself; else id of the marked set applied

@@ -109,3 +109,57 @@ def test_gate_bitmask_and_empty(B):
         st.iterate_gate(mk, 3)
         ref = oracle.grover_gate(psi0.copy(), n, mlist, 3)
         assert np.max(np.abs(to_np(st) - ref)) <= tol("c128", n, 3)
+
+
+# ---- tensor-core engine (complex64, n >= 13) ------------------------------------------
+def tc_tol(n, k):
+    """Per pass, every output sums K = 128 products in the tensor core's FP32
+    accumulator (K/16 accumulation steps of one MMA each, which may truncate),
+    then the epilogue rounds at most 3 times: |err| <= (K/16 + 3) u sum_k |x_k|,
+    and sum_k |x_k| <= sqrt(K) for a unit-norm state."""
+    passes = 2 * ((n + 6) // 7)
+    K = 128
+    return k * passes * (K / 16 + 3) * 2.0 ** -24 * K ** 0.5
+
+
+@pytest.mark.parametrize("n,m,k", [(13, 2, 2), (14, 1, 3), (15, 2, 1), (16, 3, 2), (20, 1, 2), (22, 4, 1)])
+def test_gate_tensor_cores(B, n, m, k):
+    marked = inputs.marked_indices(n, m, seed=600 + n)
+    psi0 = inputs.gaussian_state(n, seed=601 + n).astype(np.complex64).astype(np.complex128)
+    mk = B.Marked(n, marked)
+    tc = B.State(n, "c64")
+    tc.set_gate_engine(1)
+    tc.init_state(psi0)
+    tc.iterate_gate(mk, k)
+    tc.sync()
+    got = to_np(tc)
+    ref = oracle.grover_gate(psi0.copy(), n, marked, k)
+    assert np.max(np.abs(got - ref)) <= tc_tol(n, k)
+
+
+def test_gate_tensor_cores_uniform_success(B):
+    n, m = 16, 1
+    marked = inputs.marked_indices(n, m, seed=7)
+    k = B.grover_optimal_iterations(n, m)
+    mk = B.Marked(n, marked)
+    st = B.State(n, "c64")
+    st.set_gate_engine(1)
+    st.init_uniform()
+    st.iterate_gate(mk, k)
+    ps, _ = st.success_prob(mk)
+    st.sync()
+    ref = oracle.grover_operator(oracle.init_uniform(n), n, marked, k)
+    assert abs(ps - oracle.success_prob(ref, n, marked)) <= 1e-4
+    idx, _ = st.measure_topm(1)
+    assert int(idx[0]) == int(marked[0])
+
+
+def test_gate_tensor_engine_refuses(B):
+    st = B.State(12, "c64")
+    st.set_gate_engine(1)
+    with pytest.raises(B.GroverError):
+        st.iterate_gate(B.Marked(12, [1]), 1)
+    st2 = B.State(14, "c128")
+    st2.set_gate_engine(1)
+    with pytest.raises(B.GroverError):
+        st2.iterate_gate(B.Marked(14, [1]), 1)
