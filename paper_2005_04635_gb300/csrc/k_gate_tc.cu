@@ -12,18 +12,29 @@
 //     amplitudes (column = (block, re/im)); D = W X, so TMEM lane = output mid
 //     and each thread stores (re, im) pairs, 256 contiguous bytes per warp.
 // W is exact in bf16.  Each FP32 amplitude is split into three bf16 slices
-// x = b0 + b1 + b2 (each the round-to-nearest of the remainder), and the three
-// slice products accumulate into one FP32 accumulator in tensor memory.
-// Operands live in shared memory in the no-swizzle K-major layout (8 x 16-byte
-// core matrices; leading byte offset = 128 B between core matrices along K,
-// stride byte offset = 8-row group stride); one thread issues
-// 3 x K/16 tcgen05.mma (M = 128, N = K or 128, K = 16 each) and a
-// tcgen05.commit to an mbarrier; the epilogue reads the accumulator with
-// tcgen05.ld, applies the pass scale (exact power of two) and the phase shift
-// 2|0><0| - I where asked, and stores.  Every wait on the mbarrier is bounded:
-// on expiry the kernel sets the status word, frees its tensor memory and
+// x = b0 + b1 + b2 (each the round-to-nearest of the remainder); each slice
+// product has its own FP32 accumulator in tensor memory, and the epilogue adds
+// them smallest first with round to nearest.
+// Pipeline per CTA (one per SM): the next tile streams into an fp32 staging
+// buffer by TMA (one tiled cp.async.bulk.tensor copy per upper-group tile,
+// four bulk copies for a contiguous lowest-group tile; mbarrier transaction
+// count) while the current tile is multiplied and stored.  Operands live in shared memory in
+// the no-swizzle K-major layout (8 x 16-byte core matrices; leading byte
+// offset = 128 B between core matrices along K, stride byte offset = 8-row
+// group stride); one thread issues 3 x K/16 tcgen05.mma (M = 128, N = K or
+// 128, K = 16 each) and a tcgen05.commit to an mbarrier; the epilogue reads
+// the accumulators with tcgen05.ld, applies the pass scale (exact power of
+// two) and the phase shift 2|0><0| - I where asked, and stores.  Every
+// mbarrier wait is bounded: on expiry the kernel sets the status word, waits
+// (bounded) for its own copies and MMAs in flight, frees its tensor memory and
 // returns.
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <string.h>
+
+#include <mutex>
 
 #include "grover_internal.cuh"
 
@@ -33,7 +44,7 @@ namespace {
 constexpr int kTcThreads = 512;
 constexpr int kTcWarps = kTcThreads / 32;
 constexpr int kCols = 128;          // real columns per tile (= MMA M or N)
-constexpr uint32_t kTmemCols = 128; // accumulator columns allocated
+constexpr uint32_t kTmemCols = 512; // three accumulators of up to 128 columns
 constexpr long long kWaitLimit = 1ll << 22;  // mbarrier polls before giving up
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -96,26 +107,79 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t *v) {
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity) {
+    uint32_t done = 0;
+    for (long long it = 0; it < kWaitLimit && !done; ++it) {
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done) : "r"(su32(bar)), "r"(parity) : "memory");
+        if (!done) __nanosleep(32);
+    }
+    return done != 0;
+}
+
+// Tile geometry: first amplitude and the amplitude stride between mids.
+template <int KB, bool LOW> __device__ __forceinline__ uint64_t tile_base(uint64_t tile, int lo) {
+    constexpr int K = 1 << KB;
+    if (LOW) return tile * (uint64_t)(kCols / 2) * K;  // 64 blocks of K amplitudes
+    const uint64_t chunks = (1ull << lo) / (kCols / 2);
+    return ((tile / chunks) << (lo + KB)) | ((tile % chunks) * (kCols / 2));
+}
+
+// Warp 0 streams one tile of fp32 amplitudes into the staging buffer: the
+// lowest group is one contiguous block, an upper group K rows of 512 bytes.
+template <int KB, bool LOW>
+__device__ __forceinline__ void issue_tile_load(const float *amps, const CUtensorMap *tmap, uint64_t tile, int lo,
+                                                unsigned char *stage, unsigned long long *bar, int lane) {
+    constexpr int K = 1 << KB;
+    constexpr uint32_t ROWB = (kCols / 2) * 8;  // 512 bytes: 64 complex64
+    constexpr uint32_t TILEB = (uint32_t)K * ROWB;
+    const uint64_t abase = tile_base<KB, LOW>(tile, lo);
+    if (lane == 0)
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(TILEB) : "memory");
+    __syncwarp();
+    if (LOW) {
+        constexpr uint32_t PART = TILEB / 4;
+        if (lane < 4) {
+            const float *src = amps + 2 * abase + (size_t)lane * (PART / 4);
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                         ::"r"(su32(stage + lane * PART)), "l"(src), "r"(PART), "r"(su32(bar)) : "memory");
+        }
+    } else if (lane == 0) {
+        // one tiled copy: box {128 floats, K mids, 1 outer} of the view
+        // [outer][mid][2^(lo+1) floats]; x = chunk * 128 floats (a multiple of
+        // 16 bytes), y = 0, z = outer
+        const uint64_t chunks = (1ull << lo) / (kCols / 2);
+        const int x = (int)((tile % chunks) * kCols), z = (int)(tile / chunks);
+        asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+                     "[%0], [%1, {%2, %3, %4}], [%5];"
+                     ::"r"(su32(stage)), "l"(tmap), "r"(x), "r"(0), "r"(z), "r"(su32(bar)) : "memory");
+    }
+    (void)amps;
+}
+
 template <int KB, bool LOW>
 __global__ void __launch_bounds__(kTcThreads, 1)
-k_wht_tc(float *amps, int lo, uint64_t ntiles, float scale, int negate_but_zero, int *status) {
+k_wht_tc(float *amps, const __grid_constant__ CUtensorMap tmap, int lo, uint64_t ntiles, float scale,
+         int negate_but_zero, int *status) {
     constexpr int K = 1 << KB;
-    constexpr size_t SLICE = (size_t)kCols * K * 2;  // bytes of one bf16 slice of the tile
+    constexpr size_t STAGE = (size_t)K * (kCols / 2) * 8;  // fp32 tile
+    constexpr size_t SLICE = (size_t)kCols * K * 2;        // one bf16 slice of the tile
     constexpr uint32_t SBO = (K / 8) * 128;
     constexpr uint32_t LBO = 128;
     constexpr int M_MMA = 128;
     constexpr int N_MMA = LOW ? kCols : K;
     static_assert(!LOW || KB == 7, "the lowest group uses W as the 128-row operand");
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char *xs = smem;                 // [3][SLICE] state slices
-    unsigned char *ws = smem + 3 * SLICE;     // W, K x K bf16
-    __shared__ __align__(8) unsigned long long bar;
+    unsigned char *stage = smem;                        // fp32 tile from global
+    unsigned char *xs = smem + STAGE;                   // [3][SLICE] bf16 slices
+    unsigned char *ws = smem + STAGE + 3 * SLICE;       // W, K x K bf16
+    __shared__ __align__(8) unsigned long long tma_bar, mma_bar;
     __shared__ uint32_t tslot;
     __shared__ int s_abort;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // W[n][k] = (-1)^popcount(n & k), K-major
-    for (int i = tid; i < K * K / 8; i += kTcThreads) {
+    for (int i = tid; i < K * K / 8; i += kTcThreads) {  // W[n][k] = (-1)^popcount(n & k)
         const int n = i / (K / 8), k0 = (i % (K / 8)) * 8;
         float v[8];
 #pragma unroll
@@ -129,7 +193,8 @@ k_wht_tc(float *amps, int lo, uint64_t ntiles, float scale, int negate_but_zero,
     }
     if (tid == 0) {
         s_abort = 0;
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&tma_bar)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&mma_bar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -137,34 +202,37 @@ k_wht_tc(float *amps, int lo, uint64_t ntiles, float scale, int negate_but_zero,
                      "r"(kTmemCols) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     fence_before();
     __syncthreads();
     fence_after();
     const uint32_t taddr = tslot;
-    uint32_t phase = 0;
+    // loads_done / mmas_done count completed phases of the two mbarriers; the
+    // parity of the next phase to wait for is the count's low bit
+    uint32_t loads_done = 0, mmas_done = 0;
+    bool load_pending = blockIdx.x < ntiles, mma_pending = false;
+    if (warp == 0 && load_pending) issue_tile_load<KB, LOW>(amps, &tmap, blockIdx.x, lo, stage, &tma_bar, lane);
 
     for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        // ---- tile geometry (amplitude indices) ----
-        uint64_t abase;       // first amplitude of the tile
-        uint64_t mid_stride;  // amplitude stride between consecutive mids
-        if (LOW) {
-            abase = tile * (uint64_t)(kCols / 2) * K;  // 64 blocks of K amplitudes
-            mid_stride = 1;
-        } else {
-            const uint64_t chunks = (1ull << lo) / (kCols / 2);
-            abase = ((tile / chunks) << (lo + KB)) | ((tile % chunks) * (kCols / 2));
-            mid_stride = 1ull << lo;
+        const uint64_t abase = tile_base<KB, LOW>(tile, lo);
+        // ---- staged fp32 tile -> three bf16 slices ----
+        if (!mbar_wait(&tma_bar, loads_done & 1)) {
+            atomicExch(status, 2);
+            s_abort = 1;
         }
-        // ---- producer: global fp32 -> three bf16 slices in shared memory ----
+        __syncthreads();
+        if (s_abort) break;
+        ++loads_done;
+        load_pending = false;
         if (LOW) {
-            // unit = (block o of 64, k-group of 8 mids): 8 complex = 4 float4 contiguous
+            // unit = (block o, k-group of 8 mids): 8 complex = 4 float4 contiguous
             for (int u = tid; u < (kCols / 2) * (K / 8); u += kTcThreads) {
                 const int kg = u % (K / 8), o = u / (K / 8);
-                const float4 *src = reinterpret_cast<const float4 *>(amps + 2 * (abase + (uint64_t)o * K + kg * 8));
+                const float4 *src = reinterpret_cast<const float4 *>(stage) + (size_t)o * (K / 2) + kg * 4;
                 float re[8], im[8];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const float4 c = __ldcs(src + q);
+                    const float4 c = src[q];
                     re[2 * q] = c.x;
                     im[2 * q] = c.y;
                     re[2 * q + 1] = c.z;
@@ -174,14 +242,13 @@ k_wht_tc(float *amps, int lo, uint64_t ntiles, float scale, int negate_but_zero,
                 put8(xs, SLICE, 2 * o + 1, kg * 8, K, im);
             }
         } else {
-            // unit = (k-group of 8 mids, float4 column group): 8 rows x 16 bytes
+            // unit = (k-group of 8 mids, float4 column group)
             for (int u = tid; u < (K / 8) * (kCols / 4); u += kTcThreads) {
                 const int c4 = u % (kCols / 4), kg = u / (kCols / 4);
                 float col[4][8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    const uint64_t a = abase + (uint64_t)(kg * 8 + j) * mid_stride;
-                    const float4 c = __ldcs(reinterpret_cast<const float4 *>(amps + 2 * a) + c4);
+                    const float4 c = reinterpret_cast<const float4 *>(stage)[(size_t)(kg * 8 + j) * (kCols / 4) + c4];
                     col[0][j] = c.x;
                     col[1][j] = c.y;
                     col[2][j] = c.z;
@@ -195,7 +262,11 @@ k_wht_tc(float *amps, int lo, uint64_t ntiles, float scale, int negate_but_zero,
         fence_before();
         __syncthreads();
         fence_after();
-        // ---- MMA: one thread issues 3 slices x K/16 steps, then commits ----
+        // ---- next tile's load overlaps this tile's MMAs and epilogue ----
+        const uint64_t next = tile + gridDim.x;
+        if (warp == 0 && next < ntiles) issue_tile_load<KB, LOW>(amps, &tmap, next, lo, stage, &tma_bar, lane);
+        load_pending = next < ntiles;
+        // ---- MMA: one accumulator per slice (TMEM columns 128 s .. 128 s + N) ----
         if (tid == 0) {
             constexpr uint32_t idesc = idesc_bf16(M_MMA, N_MMA);
 #pragma unroll 1
@@ -206,60 +277,61 @@ k_wht_tc(float *amps, int lo, uint64_t ntiles, float scale, int negate_but_zero,
                     const uint32_t wa = su32(ws) + kk * 2 * LBO;
                     const uint64_t da = LOW ? smem_desc(wa, LBO, SBO) : smem_desc(xa, LBO, SBO);
                     const uint64_t db = LOW ? smem_desc(xa, LBO, SBO) : smem_desc(wa, LBO, SBO);
-                    const uint32_t acc = (s | kk) != 0;
+                    const uint32_t acc = kk != 0;
                     asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-                                 ::"r"(taddr), "l"(da), "l"(db), "r"(idesc), "r"(acc) : "memory");
+                                 ::"r"(taddr + 128u * s), "l"(da), "l"(db), "r"(idesc), "r"(acc) : "memory");
                 }
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(&bar))
-                         : "memory");
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         ::"r"(su32(&mma_bar)) : "memory");
         }
-        // ---- bounded wait for the accumulator ----
-        uint32_t done = 0;
-        for (long long it = 0; it < kWaitLimit && !done; ++it) {
-            asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                         "selp.u32 %0, 1, 0, p;\n\t}"
-                         : "=r"(done) : "r"(su32(&bar)), "r"(phase) : "memory");
-            if (!done) __nanosleep(32);
-        }
-        if (!done) {
+        mma_pending = true;
+        if (!mbar_wait(&mma_bar, mmas_done & 1)) {
             atomicExch(status, 2);
             s_abort = 1;
         }
-        phase ^= 1u;
         fence_after();
         __syncthreads();
         if (s_abort) break;
-        // ---- epilogue: TMEM -> registers -> global ----
+        ++mmas_done;
+        mma_pending = false;
+        // ---- epilogue: (acc2 + acc1) + acc0, scale, phase shift, store ----
         {
-            const int lg = warp & 3, cg = warp >> 2;  // TMEM lane group, 32-column chunk
+            const int lg = warp & 3, cg = warp >> 2;
             constexpr int NCH = N_MMA / 32;
             if (cg < NCH) {
-                uint32_t v[32];
-                tmem_ld32(taddr + ((uint32_t)(32 * lg) << 16) + (uint32_t)(32 * cg), v);
+                uint32_t a[32], b[32];
+                const uint32_t t0 = taddr + ((uint32_t)(32 * lg) << 16) + (uint32_t)(32 * cg);
+                tmem_ld32(t0 + 256u, a);
+                tmem_ld32(t0 + 128u, b);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) a[j] = __float_as_uint(__uint_as_float(a[j]) + __uint_as_float(b[j]));
+                tmem_ld32(t0, b);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) a[j] = __float_as_uint(__uint_as_float(a[j]) + __uint_as_float(b[j]));
                 const int row = 32 * lg + lane;
                 if (LOW) {
-                    // row = output mid, registers = columns 32cg .. 32cg+31 = 16 blocks x (re, im)
+                    // row = output mid, registers = 16 blocks x (re, im)
 #pragma unroll
                     for (int q = 0; q < 16; ++q) {
-                        const uint64_t a = abase + (uint64_t)(16 * cg + q) * K + row;
-                        float re = __uint_as_float(v[2 * q]) * scale, im = __uint_as_float(v[2 * q + 1]) * scale;
-                        if (negate_but_zero && a != 0) {
+                        const uint64_t a0 = abase + (uint64_t)(16 * cg + q) * K + row;
+                        float re = __uint_as_float(a[2 * q]) * scale, im = __uint_as_float(a[2 * q + 1]) * scale;
+                        if (negate_but_zero && a0 != 0) {
                             re = -re;
                             im = -im;
                         }
-                        __stcs(reinterpret_cast<float2 *>(amps) + a, make_float2(re, im));
+                        __stcs(reinterpret_cast<float2 *>(amps) + a0, make_float2(re, im));
                     }
                 } else {
-                    // row = column (re/im of amplitude row/2), registers = output mids 32cg + j
-                    const uint64_t a0 = abase + (uint64_t)(row >> 1);
+                    // row = column (re or im of amplitude row / 2), registers = output mids
+                    const uint64_t ar = abase + (uint64_t)(row >> 1);
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
-                        const uint64_t a = a0 + (uint64_t)(32 * cg + j) * mid_stride;
-                        float x = __uint_as_float(v[j]) * scale;
-                        if (negate_but_zero && a != 0) x = -x;
-                        __stcs(amps + 2 * a + (row & 1), x);
+                        const uint64_t a0 = ar + ((uint64_t)(32 * cg + j) << lo);
+                        float x = __uint_as_float(a[j]) * scale;
+                        if (negate_but_zero && a0 != 0) x = -x;
+                        __stcs(amps + 2 * a0 + (row & 1), x);
                     }
                 }
             }
@@ -268,17 +340,53 @@ k_wht_tc(float *amps, int lo, uint64_t ntiles, float scale, int negate_but_zero,
         __syncthreads();
         fence_after();
     }
+    // after an abort, wait (bounded) for this CTA's own load and MMA in flight
+    // before the tensor memory is freed and the CTA exits
+    if (tid == 0) {
+        if (load_pending) (void)mbar_wait(&tma_bar, loads_done & 1);
+        if (mma_pending) (void)mbar_wait(&mma_bar, mmas_done & 1);
+    }
     fence_before();
     __syncthreads();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kTmemCols) : "memory");
 }
 
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// View of an n-qubit complex64 state for the pass over bits [lo, lo + kb):
+// [outer][mid][2^(lo+1) floats], box {128, 2^kb, 1}.
+cudaError_t encode_upper_map(CUtensorMap *m, void *amps, int n, int lo, int kb) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint64_t inner = 1ull << (lo + 1);
+    const cuuint64_t dims[3] = {inner, 1ull << kb, 1ull << (n - lo - kb)};
+    const cuuint64_t strides[2] = {inner * 4, (inner << kb) * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)kCols, (cuuint32_t)(1u << kb), 1u};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, amps, dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <int KB, bool LOW>
 cudaError_t launch_tc_t(void *amps, int n, int lo, float scale, bool negate, int *status, cudaStream_t st,
                         const Geometry &g) {
     constexpr int K = 1 << KB;
-    const size_t smem = 3 * (size_t)kCols * K * 2 + (size_t)K * K * 2;
+    const size_t smem = (size_t)K * (kCols / 2) * 8 + 3 * (size_t)kCols * K * 2 + (size_t)K * K * 2;
     auto kern = k_wht_tc<KB, LOW>;
     static bool attr = false;
     if (!attr) {
@@ -286,11 +394,17 @@ cudaError_t launch_tc_t(void *amps, int n, int lo, float scale, bool negate, int
         if (e != cudaSuccess) return e;
         attr = true;
     }
+    CUtensorMap tmap;
+    memset(&tmap, 0, sizeof tmap);
+    if (!LOW) {
+        cudaError_t e = encode_upper_map(&tmap, amps, n, lo, KB);
+        if (e != cudaSuccess) return e;
+    }
     const uint64_t N = 1ull << n;
     const uint64_t ntiles = N / ((uint64_t)(kCols / 2) * K);
     const uint64_t grid = ntiles < (uint64_t)g.sm_count ? ntiles : (uint64_t)g.sm_count;
-    kern<<<(unsigned)grid, kTcThreads, smem, st>>>(static_cast<float *>(amps), lo, ntiles, scale, negate ? 1 : 0,
-                                                   status);
+    kern<<<(unsigned)grid, kTcThreads, smem, st>>>(static_cast<float *>(amps), tmap, lo, ntiles, scale,
+                                                   negate ? 1 : 0, status);
     return cudaGetLastError();
 }
 
