@@ -120,7 +120,17 @@ typedef enum {
      * tensor cores for complex64 states with n >= 13, CUDA cores otherwise;
      * 0 always CUDA cores; 1 the tensor cores (GROVER_EUNSUPPORTED for
      * complex128 or n < 13). */
-    GROVER_OPT_GATE_ENGINE = 1
+    GROVER_OPT_GATE_ENGINE = 1,
+    /* Polls (about 0.1 us each) a bounded device-side wait makes before it
+     * gives up; default 2^22.  A wait that gives up sets the device status
+     * word, the kernel waits (bounded) for its own copies in flight, frees its
+     * tensor memory and returns; grover_sync then returns GROVER_ETIMEOUT and
+     * the state is undefined. */
+    GROVER_OPT_WAIT_LIMIT = 2,
+    /* Test hook for that failure path: 1 makes the next tensor-core pass of
+     * grover_iterate_gate withhold its MMA completion signal, so its wait runs
+     * out (reset to 0 once used).  Not for production use. */
+    GROVER_OPT_TEST_STALL = 3
 } grover_option;
 
 /* Sets an execution option of the handle (see grover_option).  GROVER_EINVAL

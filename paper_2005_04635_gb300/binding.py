@@ -157,6 +157,10 @@ class State:
         """-1 automatic, 0 CUDA-core butterflies, 1 tensor cores (complex64, n >= 13)."""
         _check(lib().grover_set_option(self.handle, 1, int(value)), self.handle)
 
+    def set_option(self, opt: int, value: int):
+        """grover_set_option: 0 resident, 1 gate engine, 2 wait limit, 3 test stall."""
+        _check(lib().grover_set_option(self.handle, int(opt), int(value)), self.handle)
+
     def init_uniform(self):
         _check(lib().grover_init_uniform(self.handle), self.handle)
 

@@ -198,6 +198,8 @@ grover_status grover_create(grover_state **out, int n, grover_dtype dtype, void 
     s->sc.probs_tmp = nullptr;
     s->resident = -1;
     s->gate_engine = -1;
+    s->wait_limit = kDefaultWaitLimit;
+    s->test_stall = 0;
     s->mu_slot = 0;
     s->mu_valid = false;
     s->mu_key = 0;
@@ -230,12 +232,23 @@ grover_status grover_set_accum(grover_state *s, grover_accum mode) {
 
 grover_status grover_set_option(grover_state *s, grover_option opt, int64_t value) {
     if (grover_status st = check_state(s)) return st;
-    if (opt != GROVER_OPT_RESIDENT && opt != GROVER_OPT_GATE_ENGINE)
-        return fail(s, GROVER_EINVAL, "unknown option %d", (int)opt);
-    if (value < -1 || value > 1) return fail(s, GROVER_EINVAL, "option %d takes -1, 0 or 1", (int)opt);
-    if (opt == GROVER_OPT_RESIDENT) s->resident = (int)value;
-    else s->gate_engine = (int)value;
-    return GROVER_OK;
+    switch (opt) {
+    case GROVER_OPT_RESIDENT:
+    case GROVER_OPT_GATE_ENGINE:
+        if (value < -1 || value > 1) return fail(s, GROVER_EINVAL, "option %d takes -1, 0 or 1", (int)opt);
+        if (opt == GROVER_OPT_RESIDENT) s->resident = (int)value;
+        else s->gate_engine = (int)value;
+        return GROVER_OK;
+    case GROVER_OPT_WAIT_LIMIT:
+        if (value < 1) return fail(s, GROVER_EINVAL, "GROVER_OPT_WAIT_LIMIT must be positive");
+        s->wait_limit = value;
+        return GROVER_OK;
+    case GROVER_OPT_TEST_STALL:
+        if (value < 0 || value > 1) return fail(s, GROVER_EINVAL, "GROVER_OPT_TEST_STALL takes 0 or 1");
+        s->test_stall = (int)value;
+        return GROVER_OK;
+    }
+    return fail(s, GROVER_EINVAL, "unknown option %d", (int)opt);
 }
 
 grover_status grover_init_uniform(grover_state *s) {
@@ -456,7 +469,10 @@ grover_status grover_iterate_gate(grover_state *s, const grover_marked *mk, uint
             const bool first = pass < ngroups;  // first H^{(x)n}: scaled by 2^-n in total
             const bool phase = pass == ngroups - 1;
             if (tc && tc_pass_supported(s->n, lo, kb)) {
-                CK(s, launch_wht_tc_pass(s->amps, s->n, lo, kb, first, phase, s->sc.status, s->stream, s->geo),
+                const int stall = s->test_stall;
+                s->test_stall = 0;
+                CK(s, launch_wht_tc_pass(s->amps, s->n, lo, kb, first, phase, s->sc.status, s->wait_limit, stall,
+                                         s->stream, s->geo),
                    "tensor-core Walsh-Hadamard pass launch");
             } else {
                 CK(s, launch_wht_pass(s->amps, s->n, s->dtype, lo, kb, first, phase, s->stream, s->geo),

@@ -130,9 +130,12 @@ cudaError_t launch_wht_pass(void *amps, int n, grover_dtype dt, int lo, int kb, 
 // ---- conventional circuit on tensor cores (k_gate_tc.cu), complex64 ---------
 // true if a tensor-core pass exists for bits [lo, lo + kb) of an n-qubit state
 bool tc_pass_supported(int n, int lo, int kb);
-// Walsh-Hadamard pass on the tensor cores; a wait that gives up sets *status = 2
+// Walsh-Hadamard pass on the tensor cores; a wait longer than wait_limit
+// polls gives up and sets *status = 2; stall != 0 withholds the MMA
+// completion signal (test hook for that path)
 cudaError_t launch_wht_tc_pass(void *amps, int n, int lo, int kb, bool scaled, bool negate, int *status,
-                               cudaStream_t st, const Geometry &g);
+                               long long wait_limit, int stall, cudaStream_t st, const Geometry &g);
+constexpr long long kDefaultWaitLimit = 1ll << 22;  // mbarrier polls (~0.4 s)
 
 // ---- errors (grover_api.cu) ------------------------------------------------
 // Sets the message grover_last_error(NULL) returns on this host thread.
@@ -153,6 +156,8 @@ struct grover_state {
     grv::Scratch sc;
     int resident;           // -1 auto, 0 never, 1 required (grover_set_option)
     int gate_engine;        // -1 auto, 0 CUDA cores, 1 tensor cores (grover_set_option)
+    long long wait_limit;   // polls of a bounded device-side wait
+    int test_stall;         // test hook: the next tensor-core pass withholds its MMA signal
     int mu_slot;            // which mu[] holds the current mean
     bool mu_valid;          // cached mean of flip_key(c) is valid
     uint64_t mu_key;        // 0: mean of c itself; else id of the marked set applied

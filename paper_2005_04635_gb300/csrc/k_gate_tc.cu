@@ -45,7 +45,7 @@ constexpr int kTcThreads = 512;
 constexpr int kTcWarps = kTcThreads / 32;
 constexpr int kCols = 128;          // real columns per tile (= MMA M or N)
 constexpr uint32_t kTmemCols = 512; // three accumulators of up to 128 columns
-constexpr long long kWaitLimit = 1ll << 22;  // mbarrier polls before giving up
+
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -107,9 +107,9 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t *v) {
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity, long long limit) {
     uint32_t done = 0;
-    for (long long it = 0; it < kWaitLimit && !done; ++it) {
+    for (long long it = 0; it < limit && !done; ++it) {
         asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
                      "selp.u32 %0, 1, 0, p;\n\t}"
                      : "=r"(done) : "r"(su32(bar)), "r"(parity) : "memory");
@@ -161,7 +161,7 @@ __device__ __forceinline__ void issue_tile_load(const float *amps, const CUtenso
 template <int KB, bool LOW>
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_wht_tc(float *amps, const __grid_constant__ CUtensorMap tmap, int lo, uint64_t ntiles, float scale,
-         int negate_but_zero, int *status) {
+         int negate_but_zero, int *status, long long wait_limit, int stall) {
     constexpr int K = 1 << KB;
     constexpr size_t STAGE = (size_t)K * (kCols / 2) * 8;  // fp32 tile
     constexpr size_t SLICE = (size_t)kCols * K * 2;        // one bf16 slice of the tile
@@ -216,7 +216,7 @@ k_wht_tc(float *amps, const __grid_constant__ CUtensorMap tmap, int lo, uint64_t
     for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const uint64_t abase = tile_base<KB, LOW>(tile, lo);
         // ---- staged fp32 tile -> three bf16 slices ----
-        if (!mbar_wait(&tma_bar, loads_done & 1)) {
+        if (!mbar_wait(&tma_bar, loads_done & 1, wait_limit)) {
             atomicExch(status, 2);
             s_abort = 1;
         }
@@ -283,11 +283,13 @@ k_wht_tc(float *amps, const __grid_constant__ CUtensorMap tmap, int lo, uint64_t
                                  ::"r"(taddr + 128u * s), "l"(da), "l"(db), "r"(idesc), "r"(acc) : "memory");
                 }
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         ::"r"(su32(&mma_bar)) : "memory");
+            // test hook: without the commit nothing arrives on mma_bar
+            if (!stall)
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             ::"r"(su32(&mma_bar)) : "memory");
         }
         mma_pending = true;
-        if (!mbar_wait(&mma_bar, mmas_done & 1)) {
+        if (!mbar_wait(&mma_bar, mmas_done & 1, wait_limit)) {
             atomicExch(status, 2);
             s_abort = 1;
         }
@@ -343,8 +345,8 @@ k_wht_tc(float *amps, const __grid_constant__ CUtensorMap tmap, int lo, uint64_t
     // after an abort, wait (bounded) for this CTA's own load and MMA in flight
     // before the tensor memory is freed and the CTA exits
     if (tid == 0) {
-        if (load_pending) (void)mbar_wait(&tma_bar, loads_done & 1);
-        if (mma_pending) (void)mbar_wait(&mma_bar, mmas_done & 1);
+        if (load_pending) (void)mbar_wait(&tma_bar, loads_done & 1, wait_limit);
+        if (mma_pending) (void)mbar_wait(&mma_bar, mmas_done & 1, wait_limit);
     }
     fence_before();
     __syncthreads();
@@ -383,8 +385,8 @@ cudaError_t encode_upper_map(CUtensorMap *m, void *amps, int n, int lo, int kb) 
 }
 
 template <int KB, bool LOW>
-cudaError_t launch_tc_t(void *amps, int n, int lo, float scale, bool negate, int *status, cudaStream_t st,
-                        const Geometry &g) {
+cudaError_t launch_tc_t(void *amps, int n, int lo, float scale, bool negate, int *status, long long wait_limit,
+                        int stall, cudaStream_t st, const Geometry &g) {
     constexpr int K = 1 << KB;
     const size_t smem = (size_t)K * (kCols / 2) * 8 + 3 * (size_t)kCols * K * 2 + (size_t)K * K * 2;
     auto kern = k_wht_tc<KB, LOW>;
@@ -404,7 +406,7 @@ cudaError_t launch_tc_t(void *amps, int n, int lo, float scale, bool negate, int
     const uint64_t ntiles = N / ((uint64_t)(kCols / 2) * K);
     const uint64_t grid = ntiles < (uint64_t)g.sm_count ? ntiles : (uint64_t)g.sm_count;
     kern<<<(unsigned)grid, kTcThreads, smem, st>>>(static_cast<float *>(amps), tmap, lo, ntiles, scale,
-                                                   negate ? 1 : 0, status);
+                                                   negate ? 1 : 0, status, wait_limit, stall);
     return cudaGetLastError();
 }
 
@@ -416,13 +418,13 @@ bool tc_pass_supported(int n, int lo, int kb) {
 }
 
 cudaError_t launch_wht_tc_pass(void *amps, int n, int lo, int kb, bool scaled, bool negate, int *status,
-                               cudaStream_t st, const Geometry &g) {
+                               long long wait_limit, int stall, cudaStream_t st, const Geometry &g) {
     const float s = scaled ? ldexpf(1.0f, -kb) : 1.0f;
-    if (lo == 0) return launch_tc_t<7, true>(amps, n, lo, s, negate, status, st, g);
+    if (lo == 0) return launch_tc_t<7, true>(amps, n, lo, s, negate, status, wait_limit, stall, st, g);
     switch (kb) {
-    case 5: return launch_tc_t<5, false>(amps, n, lo, s, negate, status, st, g);
-    case 6: return launch_tc_t<6, false>(amps, n, lo, s, negate, status, st, g);
-    default: return launch_tc_t<7, false>(amps, n, lo, s, negate, status, st, g);
+    case 5: return launch_tc_t<5, false>(amps, n, lo, s, negate, status, wait_limit, stall, st, g);
+    case 6: return launch_tc_t<6, false>(amps, n, lo, s, negate, status, wait_limit, stall, st, g);
+    default: return launch_tc_t<7, false>(amps, n, lo, s, negate, status, wait_limit, stall, st, g);
     }
 }
 

@@ -163,3 +163,29 @@ def test_gate_tensor_engine_refuses(B):
     st2.set_gate_engine(1)
     with pytest.raises(B.GroverError):
         st2.iterate_gate(B.Marked(14, [1]), 1)
+
+
+def test_tensor_core_wait_gives_up_and_recovers(B):
+    """Failure detection without a GPU fault: the test hook withholds the MMA
+    completion signal of one tensor-core pass, its bounded wait (short limit)
+    runs out, grover_sync reports GROVER_ETIMEOUT, and the same handle then
+    runs a correct search."""
+    n = 14
+    marked = inputs.marked_indices(n, 2, seed=31)
+    mk = B.Marked(n, marked)
+    st = B.State(n, "c64")
+    st.set_gate_engine(1)
+    st.set_option(2, 20000)  # about 2 ms per wait
+    st.init_uniform()
+    st.set_option(3, 1)
+    st.iterate_gate(mk, 1)
+    with pytest.raises(B.GroverError) as ei:
+        st.sync()
+    assert ei.value.status == 4  # GROVER_ETIMEOUT
+    st.sync()  # the status word was cleared
+    k = B.grover_optimal_iterations(n, 2)
+    st.init_uniform()
+    st.iterate_gate(mk, k)
+    st.sync()
+    ref = oracle.grover_operator(oracle.init_uniform(n), n, marked, k)
+    assert np.max(np.abs(to_np(st) - ref)) <= tc_tol(n, k) + (k + 1) * 2.0 ** -22
