@@ -335,6 +335,73 @@ def run_ours(args):
     return out
 
 
+# ---- precision study: FP32 storage, mean accumulation modes vs the FP64 oracle ------------------------
+PRECISION_MODES = ("fp32", "kahan", "fp64", "default", "exact")
+
+
+def run_precision_study(args):
+    """n=26 i.i.d. complex Gaussian start (unit norm), M=8, 3000 iterations,
+    complex64 storage under every mean accumulation mode, complex128 for
+    comparison; errors against the FP64 oracle's closed form for an arbitrary
+    start (the rotation of the marked / unmarked means, O(N) for any k).  The
+    mean of a Gaussian start is tiny, so the same runs from the uniform start
+    (where the mean is ~1/sqrt(N) and the run passes the optimum, k = 2274) show
+    how the accumulation modes differ."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2005_04635_gb300 import binding, inputs
+    torch.cuda.set_device(0)
+    binding.lib()
+    n, m, k, seed = 26, 8, 3000, 2608
+    marked = inputs.marked_indices(n, m, seed)
+    psi = inputs.gaussian_state(n, seed + 1)
+    psi32 = psi.astype(np.complex64)
+    ref = oracle.closed_form_general(psi32.astype(np.complex128), n, marked, k)
+    ref128 = oracle.closed_form_general(psi.copy(), n, marked, k)
+    p_ref = oracle.success_prob(ref, n, marked)
+    mk = binding.Marked(n, marked)
+    rows = []
+    a_m, a_u = oracle.closed_form_uniform(n, m, k)
+    mask = np.zeros(1 << n, dtype=bool)
+    mask[marked.astype(np.int64)] = True
+    for start in ("gaussian", "uniform"):
+        for dtype, mode in [("c64", md) for md in PRECISION_MODES] + [("c128", "default")]:
+            st = binding.State(n, dtype)
+            if mode != "default":
+                st.set_accum(mode)
+            st.set_resident(0)
+            if start == "gaussian":
+                st.init_state(psi32 if dtype == "c64" else psi)
+            else:
+                st.init_uniform()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            st.iterate(mk, k)
+            e1.record()
+            ps, nrm = st.success_prob(mk)
+            got = st.amps.cpu().numpy().astype(np.complex128)
+            if start == "gaussian":
+                r = ref if dtype == "c64" else ref128
+                pr = oracle.success_prob(r, n, marked)
+                err = float(np.max(np.abs(got - r)))
+            else:
+                pr = m * a_m * a_m
+                err = float(max(np.max(np.abs(got[mask] - a_m)), np.max(np.abs(got[~mask] - a_u))))
+            rows.append({"start": start, "state": dtype, "accumulation": mode, "max_abs_err": err,
+                         "p_success": ps, "p_success_err": abs(ps - pr), "norm_err": abs(1.0 - nrm),
+                         "iteration_us": e0.elapsed_time(e1) * 1e3 / k,
+                         "value": (1 << n) * k / (e0.elapsed_time(e1) / 1e3)})
+            del st, got
+            torch.cuda.empty_cache()
+    return {"study": "precision", "workload": f"n={n}, M={m} (seed {seed}), {k} iterations; complex Gaussian "
+            f"start (seed {seed + 1}) as specified, and the uniform start for contrast",
+            "p_success_fp64": {"gaussian": p_ref, "uniform": m * a_m * a_m},
+            "bound_max_abs_fp32": 3 * k * 2.0 ** -24, "rows": rows}
+
+
 # ---- reference arm: the oracle on the host cores -----------------------------------------------------
 def run_reference(args):
     rank, world, local = dist_env()
@@ -371,6 +438,8 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--study", choices=["precision"], default=None,
+                    help="run a study instead of the throughput benchmark")
     ap.add_argument("--gate-iters", type=int, default=2,
                     help="iterations of the conventional circuit timed for comparison (0: skip)")
     ap.add_argument("--path", choices=["auto", "pass", "resident"], default="auto",
@@ -378,7 +447,10 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    out = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if args.study == "precision":
+        out = run_precision_study(args)
+    else:
+        out = run_reference(args) if args.impl == "reference" else run_ours(args)
     if out is not None:
         print(json.dumps(out), flush=True)
     try:
