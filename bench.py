@@ -335,6 +335,100 @@ def run_ours(args):
     return out
 
 
+# ---- batched: 4096 independent searches in one persistent launch --------------------------------------
+def batched_instances(count=4096, seed=4096):
+    """n ~ U[8, 20], M ~ U[1, 8] seeded marked indices, k = floor(pi/4 sqrt(N/M))."""
+    import math
+    from paper_2005_04635_gb300 import inputs
+    g = inputs.rng(seed)
+    ns = [int(x) for x in g.integers(8, 21, count)]
+    ms = [int(x) for x in g.integers(1, 9, count)]
+    marks = [inputs.marked_indices(n, m, seed * 10007 + i) for i, (n, m) in enumerate(zip(ns, ms))]
+    ks = [int(math.floor(0.78539816339744830962 * math.sqrt((1 << n) / m))) for n, m in zip(ns, ms)]
+    return ns, ks, marks
+
+
+def run_batched(args):
+    import math
+
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    from paper_2005_04635_gb300 import binding
+    binding.lib()
+    ns, ks, marks = batched_instances()
+    stream = torch.cuda.current_stream()
+    b = binding.Batch(ns, ks, marks, stream=stream)
+    threads, onchip = b.tune()
+    for _ in range(args.warmup):
+        b.run()
+    b.success()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        b.run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    p = b.success()
+    elapsed = e0.elapsed_time(e1) / 1e3
+    units = float(sum((1 << n) * k for n, k in zip(ns, ks))) * args.steps
+    t_max, units_all = aggregate(elapsed, units, backend_device=torch.device("cuda", torch.cuda.current_device()))
+    # end to end: instance tables from the host, results back to the host
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 3))
+    for _ in range(e2e_steps):
+        b2 = binding.Batch(ns, ks, marks, stream=stream)
+        b2.run()
+        b2.success()
+        b2.close()
+    torch.cuda.synchronize()
+    e2e_t = time.perf_counter() - t0
+    if rank != 0:
+        return None
+    # closed-form check of every instance's success probability
+    worst = 0.0
+    for n, k, mk, pi in zip(ns, ks, marks, p):
+        theta = math.atan2(math.sqrt(len(mk)), math.sqrt((1 << n) - len(mk)))
+        worst = max(worst, abs(pi - math.sin((2 * k + 1) * theta) ** 2))
+    # HBM bytes: streamed instances read + write every iteration; on-chip ones
+    # are written once at the end
+    onchip_amps = 2 * onchip
+    hbm = sum(16 * (1 << n) * k + 8 * (1 << n) if (1 << n) > onchip_amps else 8 * (1 << n) for n, k in zip(ns, ks))
+    peaks, peak_src = measured_peaks()
+    achieved = hbm * args.steps / t_max / 1e9
+    h2d = 4 * len(ns) + 8 * len(ns) + 8 * sum(len(x) for x in marks) + 8 * (len(ns) + 1)
+    return {
+        "metric": METRIC, "value": units_all / t_max, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (4096 seeded instances, uniform initial states)",
+        "config": {"workload": "batched: 4096 independent searches, n ~ U[8,20], M ~ U[1,8], k_i optimal, "
+                               "complex64, one persistent CUDA-graph launch per step", "name": "batched-4096",
+                   "instances": len(ns), "amp_updates_per_step": units / args.steps,
+                   "tuned": {"threads": threads, "onchip_vecs": onchip},
+                   "l2": "per-step traffic 16 B x N x k of the streamed instances (> L2 in total)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "k_batch",
+                     "algorithmic_bytes_per_launch": hbm, "peak_source": f"{peak_src} hbm_gbs",
+                     "note": "instances up to the tuned on-chip size run from shared memory and add no HBM bytes"},
+        "e2e": {"value": float(sum((1 << n) * k for n, k in zip(ns, ks))) * e2e_steps / e2e_t, "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8 * len(ns), "steps": e2e_steps},
+        "gpu_launches": args.steps, "clocks": clk,
+        "result_check": {"max_abs_p_success_error_vs_closed_form": worst},
+    }
+
+
 # ---- precision study: FP32 storage, mean accumulation modes vs the FP64 oracle ------------------------
 PRECISION_MODES = ("fp32", "kahan", "fp64", "default", "exact")
 
@@ -409,6 +503,8 @@ def run_reference(args):
         return None
     import oracle
     from paper_2005_04635_gb300 import inputs
+    if args.workload == "batched-4096":
+        return run_reference_batched(args, world)
     w = workload(args.workload)
     n_s, iters = 24, 2  # bounded sample of the workload: 2^24 amplitudes, 2 iterations per step
     marked = inputs.marked_indices(n_s, min(w["M"], 1 << n_s), w["seed"])
@@ -430,13 +526,42 @@ def run_reference(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_reference_batched(args, world):
+    """The oracle on a bounded sample of the batched workload: per step, the
+    first instances of the seeded batch with n <= 14, run to their optimal k."""
+    import oracle
+    ns, ks, marks = batched_instances()
+    sample = [(n, k, mk) for n, k, mk in zip(ns, ks, marks) if n <= 14][:24]
+
+    def step():
+        for n, k, mk in sample:
+            oracle.grover_operator(oracle.init_uniform(n), n, mk, k)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    units = float(sum((1 << n) * k for n, k, _ in sample)) * args.steps
+    value = units / dt
+    desc = f"each step: {len(sample)} instances of the seeded batch with n <= 14, FP64 operator oracle, one thread"
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (4096 seeded instances, uniform initial states)",
+            "config": {"workload": "batched: 4096 independent searches, n ~ U[8,20], M ~ U[1,8]", "name": "batched-4096"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched-4096"], default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--study", choices=["precision"], default=None,
                     help="run a study instead of the throughput benchmark")
@@ -449,6 +574,8 @@ def main(argv=None):
         ap.error("--warmup must be >= 3")
     if args.study == "precision":
         out = run_precision_study(args)
+    elif args.workload == "batched-4096" and args.impl != "reference":
+        out = run_batched(args)
     else:
         out = run_reference(args) if args.impl == "reference" else run_ours(args)
     if out is not None:

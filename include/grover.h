@@ -226,6 +226,48 @@ grover_status grover_measure_topm(grover_state *s, size_t m, uint64_t *idx, doub
 grover_status grover_success_prob(grover_state *s, const grover_marked *mk,
                                   double *p_success, double *norm);
 
+/* ---- many independent searches in one launch ---------------------------- */
+
+typedef struct grover_batch grover_batch; /* opaque: instance table, CUDA graph of the launch */
+
+/* Amplitudes (complex64) a batch of `count` instances of n_qubits[i] qubits
+ * needs: sum of 2^n_qubits[i]; 0 if some n is outside [1, 26]. */
+uint64_t grover_batch_amps_needed(size_t count, const int *n_qubits);
+
+/* Describes `count` independent searches, each the proposed grover_search
+ * (section "Proposed Simulation Method") from the uniform state: instance i
+ * has n_qubits[i] in [1, 26], k[i] iterations and the marked indices
+ * marked[marked_offsets[i] .. marked_offsets[i+1]) (host arrays; each list
+ * strictly increasing, < 2^n_qubits[i], at most 64 indices;
+ * marked_offsets[0] = 0).  dev_amps is a caller-owned device buffer of
+ * amps_capacity complex64 amplitudes, 16-byte aligned, at least
+ * grover_batch_amps_needed(); instance i's state occupies 2^n_qubits[i]
+ * amplitudes after those of instances 0..i-1.  The library copies the tables
+ * to the device, orders the instances by decreasing N * k, and captures the
+ * single persistent launch in a CUDA graph.  Synchronous. */
+grover_status grover_batch_create(grover_batch **out, size_t count, const int *n_qubits, const uint64_t *k,
+                                  const uint64_t *marked, const uint64_t *marked_offsets, void *dev_amps,
+                                  uint64_t amps_capacity, void *cuda_stream);
+
+/* Runs every instance: one launch of the captured graph on the batch's stream
+ * (asynchronous).  A persistent grid takes instances from a work counter; one
+ * thread block runs an instance's whole search (initial state, k iterations,
+ * success probability), keeping it in shared memory when it fits the tuned
+ * threshold.  Sums are exact as in grover_iterate (complex64 default). */
+grover_status grover_batch_run(grover_batch *b);
+
+/* Times the batch under each thread count (256, 512, 1024) and on-chip
+ * threshold (32, 64, 128 KiB) and keeps the fastest (the batch runs 18 times);
+ * the choice is returned if the pointers are not NULL.  Synchronous. */
+grover_status grover_batch_tune(grover_batch *b, int *threads, uint32_t *onchip_vecs);
+
+/* Copies the count success probabilities sum_marked |c_x|^2 (FP64) of the last
+ * run to the HOST array p_success.  Synchronous. */
+grover_status grover_batch_success(grover_batch *b, double *p_success);
+
+/* Waits for the batch's stream and frees its tables.  NULL is accepted. */
+grover_status grover_batch_destroy(grover_batch *b);
+
 /* ---- iteration without device allocation -------------------------------- */
 
 /* The paper has no counterpart to this call; it exists for callers that must

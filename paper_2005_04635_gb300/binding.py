@@ -45,6 +45,12 @@ _SIGS = {
     "grover_measure_topm": (ctypes.c_int, [_vp, ctypes.c_size_t, _vp, _vp]),
     "grover_success_prob": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "grover_iterate_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t, ctypes.c_uint64, _vp]),
+    "grover_batch_amps_needed": (ctypes.c_uint64, [ctypes.c_size_t, _vp]),
+    "grover_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_size_t, _vp, _vp, _vp, _vp, _vp, ctypes.c_uint64, _vp]),
+    "grover_batch_run": (ctypes.c_int, [_vp]),
+    "grover_batch_tune": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_uint32)]),
+    "grover_batch_success": (ctypes.c_int, [_vp, _vp]),
+    "grover_batch_destroy": (ctypes.c_int, [_vp]),
     "grover_sync": (ctypes.c_int, [_vp]),
     "grover_last_error": (ctypes.c_char_p, [_vp]),
     "grover_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -214,6 +220,63 @@ class State:
     def close(self):
         if self.handle:
             _check(lib().grover_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Independent searches run in one persistent launch (complex64 states).
+
+    n, k: sequences of qubit counts and iteration counts; marked: a sequence of
+    sorted index lists.  The states live in one torch tensor (``amps``);
+    instance i occupies ``offsets[i] : offsets[i] + 2**n[i]``."""
+
+    def __init__(self, n, k, marked, stream=None, device=None):
+        import torch
+        count = len(n)
+        n_arr = np.ascontiguousarray(np.asarray(n, dtype=np.int32))
+        k_arr = np.ascontiguousarray(np.asarray(k, dtype=np.uint64))
+        lists = [np.asarray(mk, dtype=np.uint64).reshape(-1) for mk in marked]
+        offs = np.zeros(count + 1, dtype=np.uint64)
+        offs[1:] = np.cumsum([len(x) for x in lists])
+        flat = np.ascontiguousarray(np.concatenate(lists) if offs[-1] else np.zeros(1, dtype=np.uint64))
+        need = int(lib().grover_batch_amps_needed(count, n_arr.ctypes.data))
+        if need == 0:
+            raise GroverError(1, "instances need n in [1, 26]")
+        self.amps = torch.empty(need, dtype=torch.complex64, device=device or "cuda")
+        self.offsets = np.concatenate([[0], np.cumsum(1 << n_arr.astype(np.int64))])[:-1]
+        self.n, self.k, self.marked = n_arr, k_arr, lists
+        h = _vp()
+        _check(lib().grover_batch_create(ctypes.byref(h), count, n_arr.ctypes.data, k_arr.ctypes.data,
+                                         flat.ctypes.data, offs.ctypes.data, self.amps.data_ptr(), need,
+                                         _stream_ptr(stream)))
+        self.handle = h
+        self.count = count
+
+    def run(self):
+        _check(lib().grover_batch_run(self.handle))
+
+    def tune(self):
+        th, oc = ctypes.c_int(), ctypes.c_uint32()
+        _check(lib().grover_batch_tune(self.handle, ctypes.byref(th), ctypes.byref(oc)))
+        return th.value, oc.value
+
+    def success(self):
+        p = np.empty(self.count, dtype=np.float64)
+        _check(lib().grover_batch_success(self.handle, p.ctypes.data))
+        return p
+
+    def state(self, i):
+        return self.amps[int(self.offsets[i]): int(self.offsets[i]) + (1 << int(self.n[i]))]
+
+    def close(self):
+        if self.handle:
+            _check(lib().grover_batch_destroy(self.handle))
             self.handle = None
 
     def __del__(self):

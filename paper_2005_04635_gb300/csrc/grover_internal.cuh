@@ -137,6 +137,32 @@ cudaError_t launch_wht_tc_pass(void *amps, int n, int lo, int kb, bool scaled, b
                                long long wait_limit, int stall, cudaStream_t st, const Geometry &g);
 constexpr long long kDefaultWaitLimit = 1ll << 22;  // mbarrier polls (~0.4 s)
 
+// ---- batched searches (k_batch.cu) ------------------------------------------
+constexpr uint32_t kBatchMaxMarked = 64;  // marked indices per instance
+constexpr int kBatchMaxQubits = 26;
+struct BatchInst {
+    uint64_t amp_off;   // first amplitude of the instance in the batch buffer
+    uint64_t k;         // iterations
+    uint64_t mark_off;  // first marked index in the concatenated lists
+    uint32_t m;         // marked indices
+    int n;              // qubits
+};
+struct BatchLaunch {
+    float4 *amps;
+    const BatchInst *inst;
+    const uint32_t *order;  // instance indices, largest N * k first
+    uint32_t count;
+    const uint64_t *marked;
+    unsigned *next;         // work counter
+    double *psucc;          // [count] success probabilities
+    uint32_t onchip_vecs;   // instances of at most this many 16-byte vectors stay in shared memory
+    int threads;            // 256, 512 or 1024
+};
+// Sets the kernel attributes for L and returns the persistent grid size.
+cudaError_t prepare_batch(const BatchLaunch &L, int sm_count, unsigned *grid);
+// Resets the work counter and launches (capturable in a CUDA graph).
+cudaError_t enqueue_batch(const BatchLaunch &L, unsigned grid, cudaStream_t st);
+
 // ---- errors (grover_api.cu) ------------------------------------------------
 // Sets the message grover_last_error(NULL) returns on this host thread.
 void set_thread_error(const char *msg);

@@ -1,0 +1,93 @@
+"""Batched searches (grover_batch_*): every instance against the oracle's
+closed form for a uniform start (marked sin((2k+1)theta)/sqrt(M), unmarked
+cos((2k+1)theta)/sqrt(N-M)), the exact group invariant, P_success within 1e-4
+(complex64), bitwise determinism, and the autotuner."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2005_04635_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2005_04635_gb300 import binding
+    binding.lib()
+    return binding
+
+
+def make_instances(count, nlo, nhi, mmax, seed, kmode="optimal"):
+    g = inputs.rng(seed)
+    ns, ks, marks = [], [], []
+    for i in range(count):
+        n = int(g.integers(nlo, nhi + 1))
+        m = int(g.integers(1, min(mmax, 1 << n) + 1))
+        mk = inputs.marked_indices(n, m, seed * 1000 + i)
+        k = oracle.optimal_iterations(n, m) if kmode == "optimal" else int(g.integers(0, 40))
+        ns.append(n)
+        ks.append(k)
+        marks.append(mk)
+    return ns, ks, marks
+
+
+def check_instance(got, n, mk, k):
+    N = 1 << n
+    m = len(mk)
+    mask = np.zeros(N, dtype=bool)
+    mask[np.asarray(mk, dtype=np.int64)] = True
+    am, au = oracle.closed_form_uniform(n, m, k)
+    tol = 3 * max(k, 1) * 2.0 ** -24 + 1e-7
+    for grp, ref in ((got[mask], am), (got[~mask], au)):
+        if grp.size:
+            assert np.all(grp == grp[0]), (n, m, k)
+            assert abs(complex(grp[0]) - ref) <= tol, (n, m, k, grp[0], ref)
+    return m * am * am
+
+
+@pytest.mark.parametrize("kmode", ["optimal", "random"])
+def test_batch_matches_closed_form(B, kmode):
+    ns, ks, marks = make_instances(96, 1, 17, 8, seed=11 if kmode == "optimal" else 12, kmode=kmode)
+    b = B.Batch(ns, ks, marks)
+    b.run()
+    p = b.success()
+    torch.cuda.synchronize()
+    for i in range(len(ns)):
+        got = b.state(i).cpu().numpy()
+        pref = check_instance(got, ns[i], marks[i], ks[i])
+        assert abs(p[i] - pref) <= 1e-4
+
+
+def test_batch_deterministic_and_tuned(B):
+    ns, ks, marks = make_instances(64, 6, 16, 8, seed=21)
+    b = B.Batch(ns, ks, marks)
+    b.run()
+    s1 = b.amps.cpu().numpy().copy()
+    p1 = b.success()
+    threads, onchip = b.tune()
+    assert threads in (256, 512, 1024) and onchip in (2048, 4096, 8192)
+    b.run()
+    p2 = b.success()
+    s2 = b.amps.cpu().numpy()
+    for i in range(len(ns)):
+        check_instance(s2[b.offsets[i]: b.offsets[i] + (1 << ns[i])], ns[i], marks[i], ks[i])
+    assert np.max(np.abs(p1 - p2)) <= 1e-6
+    b.run()
+    assert np.array_equal(b.success(), p2) and np.array_equal(b.amps.cpu().numpy(), s2)
+
+
+def test_batch_rejects_bad_input(B):
+    with pytest.raises(B.GroverError):
+        B.Batch([5], [3], [[4, 2]])  # unsorted
+    with pytest.raises(B.GroverError):
+        B.Batch([5], [3], [[40]])  # out of range
+    with pytest.raises(B.GroverError):
+        B.Batch([27], [3], [[1]])  # n too large
+    with pytest.raises(B.GroverError):
+        B.Batch([10], [3], [list(range(65))])  # more than 64 marked
