@@ -62,6 +62,10 @@ def _load():
         "or_topm": (None, [_dp, ctypes.c_int, ctypes.c_size_t, _u64p, _dp]),
         "or_neumaier_sum": (ctypes.c_double, [_dp, ctypes.c_size_t, ctypes.c_size_t]),
         "or_set_mutation": (ctypes.c_int, [ctypes.c_int]),
+        "or_phase_grover": (None, [_dp, ctypes.c_int, _u64p, ctypes.c_size_t, _dp, _dp, ctypes.c_uint64]),
+        "or_phase_loss": (ctypes.c_double, [_dp, ctypes.c_int, _u64p, ctypes.c_size_t]),
+        "or_phase_reduced": (ctypes.c_double, [ctypes.c_int, ctypes.c_uint64, _dp, _dp, ctypes.c_uint64,
+                                               _dp, _dp, _dp, _dp]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -204,6 +208,46 @@ def topm(psi, n, m: int):
 def neumaier_sum(x) -> float:
     a = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
     return float(_load().or_neumaier_sum(_dptr(a), a.size, 1))
+
+
+# ---- generalised phase iterator (differentiation) --------------------------------
+def phase_grover(psi, n, marked, phi, vphi):
+    m = _marked(marked)
+    ph = np.ascontiguousarray(np.asarray(phi, dtype=np.float64))
+    vp = np.ascontiguousarray(np.asarray(vphi, dtype=np.float64))
+    assert ph.size == vp.size
+    _load().or_phase_grover(_dptr(_state(psi, n)), n, _u64ptr(m), m.size, _dptr(ph), _dptr(vp), ph.size)
+    return psi
+
+
+def phase_loss(psi, n, marked) -> float:
+    m = _marked(marked)
+    return float(_load().or_phase_loss(_dptr(_state(psi, n)), n, _u64ptr(m), m.size))
+
+
+def phase_reduced(n, m, phi, vphi):
+    """(loss, alpha, beta) of the two-amplitude model for a uniform start."""
+    ph = np.ascontiguousarray(np.asarray(phi, dtype=np.float64))
+    vp = np.ascontiguousarray(np.asarray(vphi, dtype=np.float64))
+    out = [ctypes.c_double() for _ in range(4)]
+    loss = _load().or_phase_reduced(n, m, _dptr(ph), _dptr(vp), ph.size, *[ctypes.byref(o) for o in out])
+    return float(loss), complex(out[0].value, out[1].value), complex(out[2].value, out[3].value)
+
+
+def phase_grad_fd(loss_fn, phi, vphi, h=1e-6):
+    """Central finite differences of loss_fn(phi, vphi) in FP64."""
+    phi = np.asarray(phi, dtype=np.float64)
+    vphi = np.asarray(vphi, dtype=np.float64)
+    g1, g2 = np.zeros_like(phi), np.zeros_like(vphi)
+    for t in range(phi.size):
+        for arr, g in ((phi, g1), (vphi, g2)):
+            a = arr.copy()
+            a[t] += h
+            up = loss_fn(a, vphi) if arr is phi else loss_fn(phi, a)
+            a[t] -= 2 * h
+            dn = loss_fn(a, vphi) if arr is phi else loss_fn(phi, a)
+            g[t] = (up - dn) / (2 * h)
+    return g1, g2
 
 
 class mutation:

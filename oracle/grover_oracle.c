@@ -318,3 +318,59 @@ void or_topm(const double *psi, int n, size_t m, uint64_t *idx, double *p) {
         if (have < m) ++have;
     }
 }
+
+/* ---------------------------------------------------------------------- */
+/* Generalised phase iterator: O(phi) multiplies the marked amplitudes by
+ * e^{i phi}; D(vphi) = I + (e^{i vphi} - 1)|s><s|, i.e. c_i <- c_i -
+ * (1 - e^{i vphi}) <c> with <c> the complex mean. */
+void or_phase_grover(double *psi, int n, const uint64_t *marked, size_t m, const double *phi,
+                     const double *vphi, uint64_t K) {
+    uint64_t N = dim(n);
+    for (uint64_t t = 0; t < K; ++t) {
+        double cr = cos(phi[t]), sr = sin(phi[t]);
+        for (size_t i = 0; i < m; ++i) {
+            uint64_t x = marked[i];
+            double re = psi[2 * x], im = psi[2 * x + 1];
+            psi[2 * x] = cr * re - sr * im;
+            psi[2 * x + 1] = sr * re + cr * im;
+        }
+        double mu_re, mu_im;
+        or_mean(psi, n, &mu_re, &mu_im);
+        /* kappa = (1 - e^{i vphi}) mu */
+        double ar = 1.0 - cos(vphi[t]), ai = -sin(vphi[t]);
+        double kr = ar * mu_re - ai * mu_im, ki = ar * mu_im + ai * mu_re;
+        for (uint64_t x = 0; x < N; ++x) {
+            psi[2 * x] -= kr;
+            psi[2 * x + 1] -= ki;
+        }
+    }
+}
+
+double or_phase_loss(const double *psi, int n, const uint64_t *marked, size_t m) {
+    return -log(or_success_prob(psi, n, marked, m));
+}
+
+double or_phase_reduced(int n, uint64_t m, const double *phi, const double *vphi, uint64_t K,
+                        double *alpha_re, double *alpha_im, double *beta_re, double *beta_im) {
+    double N = (double)dim(n), M = (double)m;
+    double a0 = 1.0 / sqrt(N);
+    double ar = a0, ai = 0.0, br = a0, bi = 0.0;
+    for (uint64_t t = 0; t < K; ++t) {
+        double cr = cos(phi[t]), sr = sin(phi[t]);
+        double nr = cr * ar - sr * ai, ni = sr * ar + cr * ai;
+        ar = nr;
+        ai = ni;
+        double mu_re = (M * ar + (N - M) * br) / N, mu_im = (M * ai + (N - M) * bi) / N;
+        double qr = 1.0 - cos(vphi[t]), qi = -sin(vphi[t]);
+        double kr = qr * mu_re - qi * mu_im, ki = qr * mu_im + qi * mu_re;
+        ar -= kr;
+        ai -= ki;
+        br -= kr;
+        bi -= ki;
+    }
+    *alpha_re = ar;
+    *alpha_im = ai;
+    *beta_re = br;
+    *beta_im = bi;
+    return -log(M * (ar * ar + ai * ai));
+}

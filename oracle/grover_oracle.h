@@ -95,6 +95,21 @@ void or_topm(const double *psi, int n, size_t m, uint64_t *idx, double *p);
  * in that order. */
 double or_neumaier_sum(const double *x, size_t count, size_t stride);
 
+/* ---- generalised phase iterator (differentiation; not in the paper) ----- */
+/* Oracle O(phi): c_x <- e^{i phi} c_x for marked x.  Diffusion D(vphi):
+ * c_i <- c_i - (1 - e^{i vphi}) <c>.  At phi = vphi = pi, D(pi) O(pi) is -1
+ * times the paper's Grover iterator G.  K iterations with per-iteration
+ * phases phi[t], vphi[t] (t = 0..K-1), in place. */
+void or_phase_grover(double *psi, int n, const uint64_t *marked, size_t m, const double *phi,
+                     const double *vphi, uint64_t K);
+/* Loss -log sum_marked |c_x|^2. */
+double or_phase_loss(const double *psi, int n, const uint64_t *marked, size_t m);
+/* The same iterator from the uniform state, reduced to the two amplitudes
+ * alpha (every marked one) and beta (every unmarked one), which is exact for
+ * a uniform start; returns the loss -log(M |alpha|^2), alpha and beta. */
+double or_phase_reduced(int n, uint64_t m, const double *phi, const double *vphi, uint64_t K,
+                        double *alpha_re, double *alpha_im, double *beta_re, double *beta_im);
+
 /* ---- test hook ---------------------------------------------------------- */
 /* Plants one known mistake (for tests that show the pins catch it):
  *   0 none; 1 inversion loops stop at N-1; 2 phase shift I-2|0><0|;

@@ -323,3 +323,59 @@ def test_planted_mistakes_are_caught():
             caught = _pin_failures()
         assert caught, f"planted mistake {which} ({what}) passes every pin"
     assert _pin_failures() == []
+
+
+# --- generalised phase iterator (differentiation) --------------------------------------
+def test_phase_iterator_at_pi_is_minus_grover():
+    n, K = 8, 7
+    marked = inputs.marked_indices(n, 3, seed=1)
+    psi0 = inputs.gaussian_state(n, seed=2)
+    ph = np.full(K, np.pi)
+    a = oracle.phase_grover(psi0.copy(), n, marked, ph, ph)
+    b = oracle.grover_operator(psi0.copy(), n, marked, K)
+    assert np.max(np.abs(a - (-1) ** K * b)) <= 1e-13
+
+
+def test_phase_iterator_dense_unitary_and_inverse():
+    n, K = 5, 4
+    N = 1 << n
+    marked = inputs.marked_indices(n, 2, seed=3)
+    g = np.random.default_rng(4)
+    phi, vphi = g.uniform(0, 2 * np.pi, K), g.uniform(0, 2 * np.pi, K)
+    psi0 = inputs.gaussian_state(n, seed=5)
+    ref = psi0.copy()
+    for t in range(K):  # dense matrices: O = I + (e^{i phi}-1) P_m, D = I + (e^{i vphi}-1) |s><s|
+        P = np.zeros((N, N))
+        P[marked.astype(np.int64), marked.astype(np.int64)] = 1.0
+        S = np.full((N, N), 1.0 / N)
+        O = np.eye(N) + (np.exp(1j * phi[t]) - 1) * P
+        D = np.eye(N) + (np.exp(1j * vphi[t]) - 1) * S
+        ref = D @ (O @ ref)
+    got = oracle.phase_grover(psi0.copy(), n, marked, phi, vphi)
+    assert np.max(np.abs(got - ref)) <= 1e-14
+    assert abs(np.linalg.norm(got) - 1.0) <= 1e-14
+    back = got.copy()  # inverse iterators: O(-phi), D(-vphi) in reverse order
+    for t in reversed(range(K)):
+        oracle.phase_grover(back, n, [], [0.0], [-vphi[t]])
+        oracle.phase_grover(back, n, marked, [-phi[t]], [0.0])
+    assert np.max(np.abs(back - psi0)) <= 1e-14
+
+
+@pytest.mark.parametrize("n,m,K", [(4, 1, 3), (9, 3, 8), (12, 3, 32)])
+def test_phase_reduced_model_matches_full_state(n, m, K):
+    marked = inputs.marked_indices(n, m, seed=n)
+    g = np.random.default_rng(n)
+    phi, vphi = g.uniform(0, 2 * np.pi, K), g.uniform(0, 2 * np.pi, K)
+    psi = oracle.phase_grover(oracle.init_uniform(n), n, marked, phi, vphi)
+    loss, alpha, beta = oracle.phase_reduced(n, m, phi, vphi)
+    mask = np.zeros(1 << n, dtype=bool)
+    mask[marked.astype(np.int64)] = True
+    assert np.max(np.abs(psi[mask] - alpha)) <= 1e-13 and np.max(np.abs(psi[~mask] - beta)) <= 1e-13
+    assert abs(loss - oracle.phase_loss(psi, n, marked)) <= 1e-12
+    # gradients by central differences agree between the two
+    fd_full = oracle.phase_grad_fd(
+        lambda a, b: oracle.phase_loss(oracle.phase_grover(oracle.init_uniform(n), n, marked, a, b), n, marked),
+        phi[:4], vphi[:4], h=1e-6) if K <= 8 else None
+    if fd_full is not None:
+        fd_red = oracle.phase_grad_fd(lambda a, b: oracle.phase_reduced(n, m, a, b)[0], phi[:4], vphi[:4], h=1e-6)
+        assert np.max(np.abs(fd_full[0] - fd_red[0])) <= 1e-7 and np.max(np.abs(fd_full[1] - fd_red[1])) <= 1e-7
