@@ -496,6 +496,126 @@ def run_precision_study(args):
             "bound_max_abs_fp32": 3 * k * 2.0 ** -24, "rows": rows}
 
 
+def run_phase_study(args):
+    """Generalised phase iterator with its adjoint: n=20, M=3, K=32, phases
+    U(0, 2 pi), uniform start, loss -log P.  Gradient errors against FP64
+    central differences (h=1e-6) of the exact two-amplitude model and against
+    central differences (h=1e-4) of the GPU loss; 200 Adam steps through the
+    torch.autograd.Function; forward / backward times per iteration next to the
+    plain iterator at n=20 (L2-resident) and n=28 (HBM-bound)."""
+    import math
+
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2005_04635_gb300 import binding, inputs
+    from paper_2005_04635_gb300.autograd import phase_search_loss
+    torch.cuda.set_device(0)
+    binding.lib()
+    n, m, K, seed = 20, 3, 32, 750
+    marked = inputs.marked_indices(n, m, seed)
+    phi0, vphi0 = inputs.uniform_phases(K, seed + 1)
+    dev = lambda a: torch.as_tensor(np.asarray(a, dtype=np.float64), device="cuda").contiguous()
+    mk = binding.Marked(n, marked)
+    st = binding.State(n, "c64")
+    stats = torch.zeros(2, dtype=torch.float64, device="cuda")
+    lam = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
+    gp = torch.empty(K, dtype=torch.float64, device="cuda")
+    gv = torch.empty(K, dtype=torch.float64, device="cuda")
+    st.init_uniform()
+    st.phase_forward(mk, dev(phi0), dev(vphi0), stats)
+    st.phase_backward(mk, dev(phi0), dev(vphi0), lam, gp, gv)
+    torch.cuda.synchronize()
+    L_ref = oracle.phase_reduced(n, m, phi0, vphi0)[0]
+    L_gpu = float(stats[1].item())
+    fp, fv = oracle.phase_grad_fd(lambda a, b: oracle.phase_reduced(n, m, a, b)[0], phi0, vphi0, h=1e-6)
+    scale = float(max(np.max(np.abs(fp)), np.max(np.abs(fv))))
+    g_phi, g_vphi = gp.cpu().numpy(), gv.cpu().numpy()
+    err_fp64 = float(max(np.max(np.abs(g_phi - fp)), np.max(np.abs(g_vphi - fv))))
+
+    def gpu_loss(a, b):
+        st.init_uniform()
+        st.phase_forward(mk, dev(a), dev(b), stats)
+        torch.cuda.synchronize()
+        return float(stats[1].item())
+
+    h, fd_err = 1e-4, 0.0
+    for t in range(K):
+        for arr, g in ((phi0, g_phi), (vphi0, g_vphi)):
+            up, dn = arr.copy(), arr.copy()
+            up[t] += h
+            dn[t] -= h
+            d = ((gpu_loss(up, vphi0) - gpu_loss(dn, vphi0)) if arr is phi0 else
+                 (gpu_loss(phi0, up) - gpu_loss(phi0, dn))) / (2 * h)
+            fd_err = max(fd_err, abs(d - g[t]))
+
+    # 200 Adam steps
+    phi = dev(phi0).requires_grad_(True)
+    vphi = dev(vphi0).requires_grad_(True)
+    opt = torch.optim.Adam([phi, vphi], lr=0.05)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(200):
+        opt.zero_grad()
+        loss = phase_search_loss(phi, vphi, st, mk)
+        loss.backward()
+        opt.step()
+    torch.cuda.synchronize()
+    adam_s = time.perf_counter() - t0
+    final = float(phase_search_loss(phi.detach(), vphi.detach(), st, mk).item())
+    final_ref = oracle.phase_reduced(n, m, phi.detach().cpu().numpy(), vphi.detach().cpu().numpy())[0]
+    theta = math.asin(math.sqrt(m / (1 << n)))
+
+    # per-iteration times: forward, backward, plain iterator (pass path)
+    def timed(fn, reps=5):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / reps
+
+    peaks, peak_src = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    sizes = []
+    for nn in (20, 28):
+        mk2 = binding.Marked(nn, inputs.marked_indices(nn, m, seed + nn))
+        s2 = binding.State(nn, "c64")
+        lam2 = torch.empty(1 << nn, dtype=torch.complex64, device="cuda")
+        p_, v_ = dev(phi0), dev(vphi0)
+        s2.init_uniform()
+        fwd = timed(lambda: s2.phase_forward(mk2, p_, v_, None))
+        bwd = timed(lambda: (s2.phase_forward(mk2, p_, v_, None),
+                             s2.phase_backward(mk2, p_, v_, lam2, gp, gv))) - fwd
+        s2.set_resident(0)
+        plain = timed(lambda: s2.iterate(mk2, K))
+        N = 1 << nn
+        row = {"n": nn, "forward_us_per_iter": fwd * 1e6 / (K + 1), "backward_us_per_iter": bwd * 1e6 / (K + 1),
+               "plain_us_per_iter": plain * 1e6 / K,
+               "forward_amp_updates_per_s": N * K / fwd, "backward_amp_updates_per_s": N * K / bwd,
+               "forward_over_plain": (fwd / (K + 1)) / (plain / K),
+               "backward_over_plain": (bwd / (K + 1)) / (plain / K)}
+        if hbm and nn >= 28:
+            row["forward_hbm_frac"] = 16.0 * N * (K + 1) / fwd / 1e9 / hbm
+            row["backward_hbm_frac"] = 32.0 * N * (K + 1) / bwd / 1e9 / hbm
+            row["peak"] = f"{hbm} GB/s ({peak_src})"
+        sizes.append(row)
+        del s2, lam2
+        torch.cuda.empty_cache()
+    return {"study": "phase", "workload": f"n={n}, M={m} (seed {seed}), K={K}, phases U(0, 2pi) (seed {seed + 1}), "
+            "uniform start, complex64",
+            "loss_gpu": L_gpu, "loss_fp64": L_ref, "loss_err": abs(L_gpu - L_ref),
+            "grad_scale": scale, "grad_max_err_vs_fp64_fd": err_fp64, "grad_max_err_vs_gpu_fd_h1e-4": fd_err,
+            "adam_steps": 200, "adam_lr": 0.05, "adam_seconds": adam_s, "loss_initial": L_ref,
+            "loss_final": final, "loss_final_fp64": final_ref, "p_final": math.exp(-final_ref),
+            "p_bound_zalka": math.sin((2 * K + 1) * theta) ** 2, "timing": sizes}
+
+
 # ---- reference arm: the oracle on the host cores -----------------------------------------------------
 def run_reference(args):
     rank, world, local = dist_env()
@@ -563,7 +683,7 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched-4096"], default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--study", choices=["precision"], default=None,
+    ap.add_argument("--study", choices=["precision", "phase"], default=None,
                     help="run a study instead of the throughput benchmark")
     ap.add_argument("--gate-iters", type=int, default=2,
                     help="iterations of the conventional circuit timed for comparison (0: skip)")
@@ -574,6 +694,8 @@ def main(argv=None):
         ap.error("--warmup must be >= 3")
     if args.study == "precision":
         out = run_precision_study(args)
+    elif args.study == "phase":
+        out = run_phase_study(args)
     elif args.workload == "batched-4096" and args.impl != "reference":
         out = run_batched(args)
     else:

@@ -299,6 +299,53 @@ grover_status grover_iterate_noalloc(void *dev_amps, int n_qubits, grover_dtype 
                                      const uint64_t *dev_marked, size_t m, uint64_t k,
                                      void *cuda_stream);
 
+/* ---- generalised phase iterator and its adjoint ------------------------- */
+
+/* A differentiable generalisation of the proposed grover_search loop (section
+ * "Proposed Simulation Method"; the paper has no phases or gradients): the
+ * oracle's sign flip becomes a phase and the inversion about the mean a
+ * partial reflection,
+ *   O(phi):  c_x <- e^{i phi} c_x for marked x        (Algorithm "n-qubit Oracle"
+ *                                                       at phi = pi),
+ *   D(vphi): c_i <- c_i - (1 - e^{i vphi}) <c>        (Algorithm "n-qubit
+ *                                                       Inversion about Mean" at
+ *                                                       vphi = pi, times -1),
+ * with <c> = (1/N) sum_i c_i.  Iteration t = 0..K-1 applies D(vphi[t]) O(phi[t]).
+ * The loss is L = -log P, P = sum over marked x of |c_x|^2 after the K
+ * iterations.  Complex64 states only; the marked set must be a list of 1 to
+ * 256 indices (grover_marked_from_list), else GROVER_EUNSUPPORTED.  Means are
+ * exact sums of the FP32 amplitudes rounded once to FP64; phase factors are
+ * computed in FP64 and applied in FP32.  One pass over the state per iteration
+ * plus one initial reduction.
+ *
+ *   phi, vphi  DEVICE arrays of K doubles (radians) on the state's device,
+ *              read by the kernels when they run (stream order).
+ *   stats      NULL or a DEVICE array of 2 doubles: receives P and L.
+ *
+ * Applies the K iterations to the handle's current state in place.  Returns
+ * after enqueueing on the handle's stream.  P = 0 gives L = +inf. */
+grover_status grover_phase_forward(grover_state *s, const grover_marked *mk, const double *phi,
+                                   const double *vphi, uint64_t K, double *stats);
+
+/* Adjoint of grover_phase_forward.  The handle's state must hold the output
+ * psi_K of a forward call with the same mk, phi, vphi and K.  Each backward
+ * pass recomputes psi_t from psi_{t+1} with the inverse iterators O(-phi[t])
+ * D(-vphi[t]) (no stored intermediate states) and carries the adjoint
+ * lambda_t = dL/d conj(psi_t) (Wirtinger derivative) through the same
+ * operators, starting from lambda_K = -(marked part of psi_K) / P.  It writes
+ *   grad_phi[t]  = dL/dphi[t]  = 2 Re(i sum_marked conj(lambda_t,x) psi_t,x),
+ *   grad_vphi[t] = dL/dvphi[t] = 2 Re(i N conj(<lambda_{t+1}>) <psi_{t+1}>).
+ *
+ *   lam        DEVICE buffer of N complex64 (16-byte aligned, not overlapping
+ *              the state), overwritten; holds lambda_0 on completion.
+ *   grad_phi, grad_vphi  DEVICE arrays of K doubles, overwritten.
+ *
+ * On completion the handle's state holds psi_0 up to FP32 rounding (about K
+ * units of roundoff).  K + 1 passes; enqueued on the handle's stream. */
+grover_status grover_phase_backward(grover_state *s, const grover_marked *mk, const double *phi,
+                                    const double *vphi, uint64_t K, void *lam, double *grad_phi,
+                                    double *grad_vphi);
+
 /* ---- synchronisation and errors ----------------------------------------- */
 
 /* Waits for the handle's stream and reads the device status word:

@@ -51,6 +51,8 @@ _SIGS = {
     "grover_batch_tune": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_uint32)]),
     "grover_batch_success": (ctypes.c_int, [_vp, _vp]),
     "grover_batch_destroy": (ctypes.c_int, [_vp]),
+    "grover_phase_forward": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_uint64, _vp]),
+    "grover_phase_backward": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_uint64, _vp, _vp, _vp]),
     "grover_sync": (ctypes.c_int, [_vp]),
     "grover_last_error": (ctypes.c_char_p, [_vp]),
     "grover_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -92,6 +94,14 @@ def _stream_ptr(stream):
     if stream is None:
         stream = torch.cuda.current_stream()
     return stream.cuda_stream
+
+
+def _dptr(t):
+    """Device pointer of a contiguous CUDA float64 tensor (None for an empty one)."""
+    import torch
+    if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA float64 tensor")
+    return t.data_ptr() if t.numel() else None
 
 
 def grover_optimal_iterations(n: int, m: int) -> int:
@@ -213,6 +223,20 @@ class State:
         _check(lib().grover_success_prob(self.handle, marked.handle, ctypes.byref(ps), ctypes.byref(nrm)),
                self.handle)
         return ps.value, nrm.value
+
+    def phase_forward(self, marked: Marked, phi, vphi, stats=None):
+        """grover_phase_forward; phi, vphi: CUDA float64 tensors of K phases,
+        stats: None or a CUDA float64 tensor of 2 (receives P and -log P)."""
+        K = int(phi.numel())
+        _check(lib().grover_phase_forward(self.handle, marked.handle, _dptr(phi), _dptr(vphi), K,
+                                          _dptr(stats) if stats is not None else None), self.handle)
+
+    def phase_backward(self, marked: Marked, phi, vphi, lam, grad_phi, grad_vphi):
+        """grover_phase_backward; lam: CUDA complex64 tensor of 2^n (overwritten
+        with lambda_0), grad_phi / grad_vphi: CUDA float64 tensors of K."""
+        K = int(phi.numel())
+        _check(lib().grover_phase_backward(self.handle, marked.handle, _dptr(phi), _dptr(vphi), K,
+                                           lam.data_ptr(), _dptr(grad_phi), _dptr(grad_vphi)), self.handle)
 
     def sync(self):
         _check(lib().grover_sync(self.handle), self.handle)

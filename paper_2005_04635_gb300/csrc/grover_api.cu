@@ -213,6 +213,7 @@ grover_status grover_destroy(grover_state *s) {
     cudaError_t e1 = cudaStreamSynchronize(s->stream);
     cudaError_t e2 = cudaFree(s->scratch_base);
     cudaError_t e3 = s->sc.probs_tmp ? cudaFree(s->sc.probs_tmp) : cudaSuccess;
+    if (s->phase_mem && e3 == cudaSuccess) e3 = cudaFree(s->phase_mem);
     free(s);
     cudaError_t e = e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "grover_destroy");

@@ -163,6 +163,43 @@ cudaError_t prepare_batch(const BatchLaunch &L, int sm_count, unsigned *grid);
 // Resets the work counter and launches (capturable in a CUDA graph).
 cudaError_t enqueue_batch(const BatchLaunch &L, unsigned grid, cudaStream_t st);
 
+// ---- generalised phase iterator and its adjoint (k_phase.cu), complex64 ----
+constexpr int kPhaseMaxGrid = 2048;  // CTAs of a phase-iterator launch
+constexpr uint64_t kPhaseMaxMarked = 256;
+// Constants one pass hands to the next (written by the pass's last CTA).
+struct PhaseConst {
+    float4 kpsi;        // kappa applied to psi as (re hi, re lo, im hi, im lo)
+    float4 klam;        // kappa applied to lambda (backward only)
+    float2 rot;         // e^{i phi} (forward) or e^{-i phi} (backward) on marked amplitudes
+    double2 mean_psi;   // mean of the state the pass produced
+    double2 mean_lam;   // mean of the adjoint the pass produced (backward only)
+    double p_success;   // sum over marked x of |psi_x|^2 (last forward pass, backward start)
+};
+struct PhaseArgs {
+    void *psi;                  // complex64 state, nvec 16-byte vectors
+    void *lam;                  // complex64 adjoint (backward)
+    uint64_t nvec;
+    int n;
+    const uint64_t *list;       // sorted marked indices
+    uint32_t m;
+    const double *phi, *vphi;   // [K] phases (device)
+    long long t;                // iteration this pass applies (forward: -1 = initial reduction)
+    long long K;
+    const PhaseConst *cin;
+    PhaseConst *cout;
+    double2 *partials;          // [3 * 2 * kPhaseMaxGrid]
+    unsigned *ticket;           // last-CTA-done counter, left at 0
+    double *grad_phi, *grad_vphi;  // [K] (backward, device)
+    double *stats;              // [2] P_success and -log P_success, or NULL (forward)
+};
+// Forward pass t (update) or the initial reduction (t = -1, no update);
+// stream: streaming cache hints (data larger than L2).
+cudaError_t launch_phase_fwd(const PhaseArgs &a, bool update, bool stream, cudaStream_t st, int sm_count);
+// Backward pass t: psi and lambda through D(-vphi_t) then O(-phi_t).
+cudaError_t launch_phase_bwd(const PhaseArgs &a, bool stream, cudaStream_t st, int sm_count);
+// lambda_K from psi_K, dL/dvphi_{K-1} and the constants of backward pass K-1.
+cudaError_t launch_phase_bwd_start(const PhaseArgs &a, bool stream, cudaStream_t st, int sm_count);
+
 // ---- errors (grover_api.cu) ------------------------------------------------
 // Sets the message grover_last_error(NULL) returns on this host thread.
 void set_thread_error(const char *msg);
@@ -187,6 +224,7 @@ struct grover_state {
     int mu_slot;            // which mu[] holds the current mean
     bool mu_valid;          // cached mean of flip_key(c) is valid
     uint64_t mu_key;        // 0: mean of c itself; else id of the marked set applied
+    void *phase_mem;        // phase-iterator scratch (allocated on first use)
     char err[512];
 };
 

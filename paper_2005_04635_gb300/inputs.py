@@ -9,7 +9,8 @@ Workload recipe (the paper fixes only "a search state |i>"; sizes follow the
 benchmark configurations):
   * marked indices: M distinct indices drawn uniformly from [0, N), sorted;
   * initial state: uniform (|0> followed by H^{(x)n}), or i.i.d. complex
-    Gaussian amplitudes (re, im ~ N(0, 1)) scaled to unit norm in FP64.
+    Gaussian amplitudes (re, im ~ N(0, 1)) scaled to unit norm in FP64;
+  * phases of the phase iterator: i.i.d. uniform on [0, 2 pi).
 """
 from __future__ import annotations
 
@@ -56,3 +57,10 @@ def gaussian_state(n: int, seed: int) -> np.ndarray:
     psi = re + 1j * im
     psi /= np.sqrt(np.sum(re * re + im * im))
     return psi.astype(np.complex128)
+
+
+def uniform_phases(K: int, seed: int) -> tuple[np.ndarray, np.ndarray]:
+    """Two arrays of K phases i.i.d. uniform on [0, 2 pi) (float64): the
+    oracle phases phi and the diffusion phases vphi of the phase iterator."""
+    g = rng(seed)
+    return g.uniform(0.0, 2.0 * np.pi, K), g.uniform(0.0, 2.0 * np.pi, K)
