@@ -379,3 +379,16 @@ def test_phase_reduced_model_matches_full_state(n, m, K):
     if fd_full is not None:
         fd_red = oracle.phase_grad_fd(lambda a, b: oracle.phase_reduced(n, m, a, b)[0], phi[:4], vphi[:4], h=1e-6)
         assert np.max(np.abs(fd_full[0] - fd_red[0])) <= 1e-7 and np.max(np.abs(fd_full[1] - fd_red[1])) <= 1e-7
+
+
+@pytest.mark.parametrize("n,m,K", [(10, 1, 25), (20, 3, 32), (30, 5, 1000)])
+def test_phase_reduced_model_at_pi_is_the_closed_form(n, m, K):
+    """At phi = vphi = pi the reduced model is (-1)^K times the textbook rotation:
+    alpha = sin((2K+1) theta) / sqrt(M), beta = cos((2K+1) theta) / sqrt(N - M)."""
+    ph = np.full(K, np.pi)
+    loss, alpha, beta = oracle.phase_reduced(n, m, ph, ph)
+    theta = math.asin(math.sqrt(m / (1 << n)))
+    a = (-1) ** K * math.sin((2 * K + 1) * theta) / math.sqrt(m)
+    b = (-1) ** K * math.cos((2 * K + 1) * theta) / math.sqrt((1 << n) - m)
+    assert abs(alpha - a) <= 1e-12 * max(1.0, abs(a)) * K and abs(beta - b) <= 1e-12 * K / math.sqrt(1 << n) + 1e-15
+    assert abs(loss + math.log(m * a * a)) <= 1e-10
