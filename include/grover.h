@@ -104,17 +104,26 @@ grover_status grover_destroy(grover_state *s);
 grover_status grover_set_accum(grover_state *s, grover_accum mode);
 
 typedef enum {
-    /* How grover_iterate runs.  The persistent on-chip iterator keeps the
-     * state in one thread-block cluster's shared memory for all k iterations;
-     * it can run when the state fits (16 CTAs x 200 KiB: n <= 18 complex64,
-     * n <= 17 complex128) and the accumulation mode is GROVER_ACC_DEFAULT or
-     * GROVER_ACC_EXACT, and it sums exactly (fixed point).
-     *   -1 (default): the persistent iterator for n <= 17 (complex64) or
-     *                 n <= 15 (complex128), where it is faster, else one fused
-     *                 pass per iteration;
+    /* How grover_iterate runs.  Two persistent iterators keep the state in
+     * shared memory for all k iterations and sum exactly (fixed point); they
+     * need GROVER_ACC_DEFAULT or GROVER_ACC_EXACT.
+     *   cluster: one thread-block cluster (16 CTAs x 200 KiB: n <= 18
+     *            complex64, n <= 17 complex128), partials exchanged through
+     *            distributed shared memory;
+     *   grid:    one CTA per SM (cooperative launch; 152 x 226 KiB on GB300:
+     *            n <= 22 complex64, n <= 21 complex128), partials exchanged
+     *            through tagged global slots with bounded waits (a wait that
+     *            runs out sets the status word: GROVER_ETIMEOUT at
+     *            grover_sync).
+     *   -1 (default): the cluster iterator for n <= 17 (complex64) or n <= 15
+     *                 (complex128); the grid iterator for 19 <= n <= 22
+     *                 (complex64) or 18 <= n <= 20 (complex128); else one
+     *                 fused pass per iteration (the faster choice at each n
+     *                 as measured on GB300);
      *    0: always one fused pass per iteration;
-     *    1: the persistent iterator wherever it can run (grover_iterate returns
-     *       GROVER_EUNSUPPORTED where it cannot). */
+     *    1: the cluster iterator where it fits, else the grid iterator
+     *       (GROVER_EUNSUPPORTED where neither fits);
+     *    2: the grid iterator (GROVER_EUNSUPPORTED where it does not fit). */
     GROVER_OPT_RESIDENT = 0,
     /* Engine of grover_iterate_gate's Walsh-Hadamard passes: -1 (default) the
      * tensor cores for complex64 states with n >= 13, CUDA cores otherwise;
@@ -127,9 +136,10 @@ typedef enum {
      * tensor memory and returns; grover_sync then returns GROVER_ETIMEOUT and
      * the state is undefined. */
     GROVER_OPT_WAIT_LIMIT = 2,
-    /* Test hook for that failure path: 1 makes the next tensor-core pass of
-     * grover_iterate_gate withhold its MMA completion signal, so its wait runs
-     * out (reset to 0 once used).  Not for production use. */
+    /* Test hook for those failure paths: 1 makes the next tensor-core pass
+     * of grover_iterate_gate withhold its MMA completion signal, or the next
+     * grid persistent iterator launch withhold CTA 0's first partial, so a
+     * wait runs out (reset to 0 once used).  Not for production use. */
     GROVER_OPT_TEST_STALL = 3
 } grover_option;
 
@@ -186,7 +196,8 @@ grover_status grover_diffuse(grover_state *s);
 /* k Grover iterations of the proposed grover_search loop: each applies the
  * oracle then the inversion about the mean, as one fused device pass over the
  * state per iteration (the mean used by iteration t+1 is accumulated while
- * iteration t stores).  k = 0 is a no-op. */
+ * iteration t stores), or inside one persistent launch for states that fit
+ * on chip (GROVER_OPT_RESIDENT).  k = 0 is a no-op. */
 grover_status grover_iterate(grover_state *s, const grover_marked *mk, uint64_t k);
 
 /* k iterations of the conventional circuit (section "Background",

@@ -166,7 +166,8 @@ class State:
         _check(lib().grover_set_accum(self.handle, ACC[mode]), self.handle)
 
     def set_resident(self, value: int):
-        """-1 automatic, 0 one pass per iteration, 1 the persistent on-chip iterator."""
+        """-1 automatic, 0 one pass per iteration, 1 a persistent iterator
+        (cluster, else grid), 2 the grid-wide persistent iterator."""
         _check(lib().grover_set_option(self.handle, 0, int(value)), self.handle)
 
     def set_gate_engine(self, value: int):

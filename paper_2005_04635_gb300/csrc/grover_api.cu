@@ -214,6 +214,7 @@ grover_status grover_destroy(grover_state *s) {
     cudaError_t e2 = cudaFree(s->scratch_base);
     cudaError_t e3 = s->sc.probs_tmp ? cudaFree(s->sc.probs_tmp) : cudaSuccess;
     if (s->phase_mem && e3 == cudaSuccess) e3 = cudaFree(s->phase_mem);
+    if (s->rg_mem && e3 == cudaSuccess) e3 = cudaFree(s->rg_mem);
     free(s);
     cudaError_t e = e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "grover_destroy");
@@ -235,10 +236,12 @@ grover_status grover_set_option(grover_state *s, grover_option opt, int64_t valu
     if (grover_status st = check_state(s)) return st;
     switch (opt) {
     case GROVER_OPT_RESIDENT:
+        if (value < -1 || value > 2) return fail(s, GROVER_EINVAL, "GROVER_OPT_RESIDENT takes -1, 0, 1 or 2");
+        s->resident = (int)value;
+        return GROVER_OK;
     case GROVER_OPT_GATE_ENGINE:
         if (value < -1 || value > 1) return fail(s, GROVER_EINVAL, "option %d takes -1, 0 or 1", (int)opt);
-        if (opt == GROVER_OPT_RESIDENT) s->resident = (int)value;
-        else s->gate_engine = (int)value;
+        s->gate_engine = (int)value;
         return GROVER_OK;
     case GROVER_OPT_WAIT_LIMIT:
         if (value < 1) return fail(s, GROVER_EINVAL, "GROVER_OPT_WAIT_LIMIT must be positive");
@@ -404,16 +407,22 @@ grover_status grover_iterate(grover_state *s, const grover_marked *mk, uint64_t 
     if (grover_status st = check_marked(s, mk)) return st;
     if (k == 0) return GROVER_OK;
     if (s->resident != 0) {
-        unsigned C = 0;
-        uint32_t nv = 0;
-        size_t smem = 0;
         const bool exact_ok = s->acc == GROVER_ACC_DEFAULT || s->acc == GROVER_ACC_EXACT;
-        // automatic choice: where one cluster beats a grid-wide pass per
-        // iteration on GB300 (measured: the cluster's 16 SMs run out of FP64
-        // and integer throughput above these sizes)
-        const int auto_max = s->dtype == GROVER_C64 ? 17 : 15;
-        const bool wanted = s->resident == 1 || s->n <= auto_max;
-        if (wanted && exact_ok && resident_plan(s->n, s->dtype, &C, &nv, &smem)) {
+        unsigned C = 0, G = 0;
+        uint32_t nv = 0, gv = 0;
+        size_t smem = 0, gsmem = 0;
+        const bool cluster_fits = exact_ok && resident_plan(s->n, s->dtype, &C, &nv, &smem);
+        const bool grid_fits = exact_ok && resident_grid_plan(s->n, s->dtype, s->geo.sm_count, &G, &gv, &gsmem);
+        // automatic choice, from per-iteration times measured on GB300: one
+        // cluster up to cluster_max; the whole grid for [grid_min, grid_max]
+        // (its exchange through global memory costs about 5.5 us per
+        // iteration, so it wins only once a pass costs more); passes otherwise
+        const bool c64 = s->dtype == GROVER_C64;
+        const int cluster_max = c64 ? 17 : 15, grid_min = c64 ? 19 : 18, grid_max = c64 ? 22 : 20;
+        const bool use_cluster = cluster_fits && (s->resident == 1 || (s->resident == -1 && s->n <= cluster_max));
+        const bool use_grid = !use_cluster && grid_fits &&
+                              (s->resident >= 1 || (s->resident == -1 && s->n >= grid_min && s->n <= grid_max));
+        if (use_cluster) {
             ResArgs r;
             r.amps = s->amps;
             r.slice_vecs = nv;
@@ -429,9 +438,36 @@ grover_status grover_iterate(grover_state *s, const grover_marked *mk, uint64_t 
             }
             (void)cudaGetLastError();
             if (s->resident == 1) return cuda_fail(s, e, "persistent iterator launch");
-        } else if (s->resident == 1 && !(exact_ok && resident_plan(s->n, s->dtype, &C, &nv, &smem))) {
-            return fail(s, GROVER_EUNSUPPORTED, "the persistent iterator needs a state of at most 16 x 200 KiB and "
-                                                "GROVER_ACC_DEFAULT or GROVER_ACC_EXACT");
+        } else if (use_grid) {
+            const size_t slot_bytes = sizeof(GridSlot) * 2 * 512;
+            if (!s->rg_mem) CK(s, cudaMalloc(&s->rg_mem, slot_bytes + 256), "cudaMalloc(grid iterator slots)");
+            ResGridArgs r;
+            r.amps = s->amps;
+            r.nvec = nvec_of(s);
+            r.slice_vecs = gv;
+            r.mk = mk->dev;
+            r.k = k;
+            r.inv_n = ldexp(1.0, -s->n);
+            r.mu_out = s->sc.mu + s->mu_slot;
+            r.slots = (GridSlot *)s->rg_mem;
+            r.counter = (unsigned long long *)((char *)s->rg_mem + slot_bytes);
+            r.status = s->sc.status;
+            r.wait_limit = s->wait_limit;
+            r.stall = s->test_stall;
+            s->test_stall = 0;
+            CK(s, cudaMemsetAsync(r.counter, 0, sizeof(unsigned long long), s->stream), "grid iterator counter reset");
+            cudaError_t e = launch_resident_grid(r, s->dtype, G, gsmem, s->stream);
+            if (e == cudaSuccess) {
+                s->mu_valid = true;
+                s->mu_key = mk->id;
+                return GROVER_OK;
+            }
+            (void)cudaGetLastError();
+            if (s->resident >= 1) return cuda_fail(s, e, "grid persistent iterator launch");
+        } else if (s->resident >= 1) {
+            return fail(s, GROVER_EUNSUPPORTED, "the persistent iterators need GROVER_ACC_DEFAULT or GROVER_ACC_EXACT "
+                                                "and a state that fits the shared memory of one cluster (16 x 200 "
+                                                "KiB) or of all SMs (%d x 226 KiB)", s->geo.sm_count);
         }
     }
     if (grover_status st = ensure_mean(s, mk->dev, mk->id)) return st;

@@ -119,6 +119,31 @@ struct ResArgs {
 // false if the state does not fit one cluster's shared memory
 bool resident_plan(int n, grover_dtype dt, unsigned *C, uint32_t *slice_vecs, size_t *smem);
 cudaError_t launch_resident(const ResArgs &a, grover_dtype dt, unsigned C, size_t smem, cudaStream_t st);
+// Grid-wide variant (cooperative launch, one CTA per SM, partials exchanged
+// through global slots and an arrival counter).
+constexpr size_t kRgSmemMax = 226 * 1024;  // dynamic shared memory per CTA
+struct GridSlot {
+    unsigned long long rl, rh, il, ih;  // exact partial (128-bit Re, Im)
+    double sr, si;                      // FP64 side sums
+    int side;
+    int pad;
+};
+struct ResGridArgs {
+    void *amps;
+    uint64_t nvec;          // 16-byte vectors in the state
+    uint32_t slice_vecs;    // vectors per CTA (the last CTA may hold fewer)
+    MarkedDev mk;
+    uint64_t k;
+    double inv_n;
+    MeanSlot *mu_out;
+    GridSlot *slots;        // [2][grid]
+    unsigned long long *counter;  // arrivals, zeroed before the launch
+    int *status;            // set to 3 if a wait runs out
+    long long wait_limit;   // polls of the counter before giving up
+    int stall;              // test hook: CTA 0 never reports its first partial
+};
+bool resident_grid_plan(int n, grover_dtype dt, int sm_count, unsigned *G, uint32_t *slice_vecs, size_t *smem);
+cudaError_t launch_resident_grid(const ResGridArgs &a, grover_dtype dt, unsigned G, size_t smem, cudaStream_t st);
 
 // ---- conventional circuit (k_gate.cu) ---------------------------------------
 // One Walsh-Hadamard pass over index bits [lo, lo + kb) (kb <= 8; lo = 0 or
@@ -225,6 +250,7 @@ struct grover_state {
     bool mu_valid;          // cached mean of flip_key(c) is valid
     uint64_t mu_key;        // 0: mean of c itself; else id of the marked set applied
     void *phase_mem;        // phase-iterator scratch (allocated on first use)
+    void *rg_mem;           // grid-resident iterator slots + counter (allocated on first use)
     char err[512];
 };
 

@@ -1,4 +1,6 @@
-// k_resident.cu -- persistent on-chip Grover iterator for small states.
+// k_resident.cu -- persistent on-chip Grover iterators for small and mid-size
+// states: one thread-block cluster (k_resident_cluster) or the whole grid
+// (k_resident_grid, further down).
 //
 // One thread-block cluster of C CTAs (C <= 16) runs all k iterations of the
 // proposed grover_search loop in one launch.  CTA r keeps amplitudes
@@ -246,6 +248,282 @@ __global__ void __launch_bounds__(kResThreads) k_resident_cluster(ResArgs a) {
     cl.sync();  // keep every CTA's partial slots alive until all have read them
 }
 
+// ---- grid-wide variant ----------------------------------------------------------------
+// The same iteration over all SMs: a cooperative launch of G CTAs (one per SM,
+// all co-resident), CTA r keeping vectors [r*L, min((r+1)*L, nvec)) in shared
+// memory.  There is no hardware barrier across the grid, so the partials are
+// exchanged through global memory: each CTA writes its exact partial to its
+// slot and adds 1 to a counter with release semantics; one thread per CTA
+// polls the counter (acquire loads, at most wait_limit polls) until all G
+// partials of the iteration are in (the counter was zeroed before the launch
+// and only grows: G * (t + 2) after iteration t), then threads 0..G-1 read
+// the G slots and the CTA adds them in rank order -- the bitwise identical
+// mean in every CTA.  Slots are double buffered by iteration parity: a CTA
+// writes a slot again only after the counter shows every CTA's next partial,
+// which each CTA adds only after it has read the slot.  A wait that runs out
+// sets *status = 3 and the CTA leaves the loop (the others then run out too).
+constexpr int kRgThreads = 512;
+constexpr int kRgWarps = kRgThreads / 32;
+
+__device__ __forceinline__ void red_release_add_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+template <class T>
+__global__ void __launch_bounds__(kRgThreads, 1) k_resident_grid(ResGridArgs a) {
+    using V = typename Vec<T>::V;
+    constexpr int APV = Vec<T>::APV;
+    constexpr int U = 4;
+    const unsigned rank = blockIdx.x, G = gridDim.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    extern __shared__ __align__(16) unsigned char smem[];
+    V *sl = reinterpret_cast<V *>(smem);
+    const uint64_t start = (uint64_t)rank * a.slice_vecs;
+    const uint32_t nv = start >= a.nvec ? 0u
+                        : (uint32_t)((a.nvec - start) < a.slice_vecs ? (a.nvec - start) : a.slice_vecs);
+    const uint32_t nbits = nv * APV, nwords = (a.slice_vecs * APV + 31) / 32;
+    uint32_t *fm = reinterpret_cast<uint32_t *>(smem + (size_t)a.slice_vecs * sizeof(V));
+    __shared__ unsigned long long wint[kRgWarps][4];
+    __shared__ double wside[kRgWarps][2];
+    __shared__ int wflag[kRgWarps];
+    __shared__ MeanSlot s_mu;
+    __shared__ int s_abort;
+
+    V *g = static_cast<V *>(a.amps) + start;
+    const uint64_t a0 = start * APV;
+    for (uint32_t j = threadIdx.x; j < nv; j += kRgThreads) sl[j] = g[j];
+    for (uint32_t w = threadIdx.x; w < nwords; w += kRgThreads) fm[w] = 0u;
+    if (threadIdx.x == 0) s_abort = 0;
+    __syncthreads();
+    if (a.mk.mode == MARK_LIST) {
+        for (uint64_t i = threadIdx.x; i < a.mk.m; i += kRgThreads) {
+            const uint64_t x = a.mk.list[i];
+            if (x >= a0 && x < a0 + nbits) atomicOr(fm + ((x - a0) >> 5), 1u << (uint32_t)((x - a0) & 31));
+        }
+    } else if (a.mk.mode == MARK_BITS) {
+        for (uint32_t e = threadIdx.x; e < nbits; e += kRgThreads) {
+            const uint64_t x = a0 + e;
+            if ((a.mk.words[x >> 5] >> (uint32_t)(x & 31)) & 1u) atomicOr(fm + (e >> 5), 1u << (e & 31));
+        }
+    }
+    __syncthreads();
+
+    for (long long t = -1; t < (long long)a.k; ++t) {
+        const bool upd = t >= 0;
+        const int par = (int)((t + 1) & 1);
+        T two_re = T(0), two_im = T(0), lo_re = T(0), lo_im = T(0);
+        if (upd) {
+            if constexpr (APV == 2) {
+                two_re = s_mu.two32.x;
+                lo_re = s_mu.two32.y;
+                two_im = s_mu.two32.z;
+                lo_im = s_mu.two32.w;
+            } else {
+                two_re = s_mu.two.x;
+                two_im = s_mu.two.y;
+            }
+        }
+        u128 ar = 0, ai = 0;
+        double sr = 0.0, si = 0.0;
+        for (uint32_t j0 = threadIdx.x; j0 < nv; j0 += U * kRgThreads) {
+            T gr[U * APV], gi[U * APV];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const uint32_t j = j0 + u * kRgThreads;
+                if (j >= nv) {
+#pragma unroll
+                    for (int q = 0; q < APV; ++q) gr[u * APV + q] = gi[u * APV + q] = T(0);
+                    continue;
+                }
+                V c = sl[j];
+                const uint32_t e = j * APV;
+                const uint32_t f = (fm[e >> 5] >> (e & 31)) & ((1u << APV) - 1u);
+                if constexpr (APV == 2) {
+                    const uint32_t f0 = f & 1u, f1 = f >> 1;
+                    if (upd) {
+                        c.x = (two_re - flip(c.x, f0)) + lo_re;
+                        c.y = (two_im - flip(c.y, f0)) + lo_im;
+                        c.z = (two_re - flip(c.z, f1)) + lo_re;
+                        c.w = (two_im - flip(c.w, f1)) + lo_im;
+                        sl[j] = c;
+                    }
+                    gr[2 * u] = flip(c.x, f0);
+                    gi[2 * u] = flip(c.y, f0);
+                    gr[2 * u + 1] = flip(c.z, f1);
+                    gi[2 * u + 1] = flip(c.w, f1);
+                } else {
+                    if (upd) {
+                        c.x = two_re - flip(c.x, f);
+                        c.y = two_im - flip(c.y, f);
+                        sl[j] = c;
+                    }
+                    gr[u] = flip(c.x, f);
+                    gi[u] = flip(c.y, f);
+                }
+            }
+            if constexpr (APV == 2) {
+                fix_add<4>(ar, sr, pairwise<U * APV>(gr));
+                fix_add<4>(ai, si, pairwise<U * APV>(gi));
+            } else {
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    fix_add<4>(ar, sr, gr[u]);
+                    fix_add<4>(ai, si, gi[u]);
+                }
+            }
+        }
+        // CTA partial (exact), written to its slot
+        ar = warp_sum_u128(ar);
+        ai = warp_sum_u128(ai);
+        const int any_side = __syncthreads_or(sr != 0.0 || si != 0.0);
+        if (any_side) {
+            sr = warp_sum(sr);
+            si = warp_sum(si);
+        }
+        if (lane == 0) {
+            wint[warp][0] = (unsigned long long)ar;
+            wint[warp][1] = (unsigned long long)(ar >> 64);
+            wint[warp][2] = (unsigned long long)ai;
+            wint[warp][3] = (unsigned long long)(ai >> 64);
+            wside[warp][0] = sr;
+            wside[warp][1] = si;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            u128 r = 0, i = 0;
+            double s1 = 0.0, s2 = 0.0;
+            if (lane < kRgWarps) {
+                r = ((u128)wint[lane][1] << 64) | wint[lane][0];
+                i = ((u128)wint[lane][3] << 64) | wint[lane][2];
+                s1 = wside[lane][0];
+                s2 = wside[lane][1];
+            }
+            r = warp_sum_u128(r);
+            i = warp_sum_u128(i);
+            if (any_side) {
+                s1 = warp_sum(s1);
+                s2 = warp_sum(s2);
+            }
+            const bool withhold = a.stall && t == -1 && rank == 0;  // test hook: this partial never arrives
+            if (lane == 0) {
+                GridSlot *p = a.slots + (size_t)par * G + rank;
+                p->rl = (unsigned long long)r;
+                p->rh = (unsigned long long)(r >> 64);
+                p->il = (unsigned long long)i;
+                p->ih = (unsigned long long)(i >> 64);
+                p->sr = s1;
+                p->si = s2;
+                p->side = any_side;
+                if (!withhold) red_release_add_u64(a.counter, 1ull);
+                // wait until the G partials of this iteration are in
+                const unsigned long long target = (unsigned long long)G * (unsigned long long)(t + 2);
+                long long polls = 0;
+                int to = 0;
+                while (ld_acquire_u64(a.counter) < target) {
+                    if (++polls >= a.wait_limit) {
+                        to = 1;
+                        break;
+                    }
+                }
+                s_abort = to;
+            }
+        }
+        __syncthreads();
+        if (s_abort) {
+            if (threadIdx.x == 0) atomicExch(a.status, 3);
+            break;
+        }
+        // gather: thread q < G reads CTA q's partial
+        u128 r = 0, i = 0;
+        double s1 = 0.0, s2 = 0.0;
+        int side = 0;
+        if (threadIdx.x < G) {
+            const GridSlot *p = a.slots + (size_t)par * G + threadIdx.x;
+            r = ((u128)__ldcg(&p->rh) << 64) | __ldcg(&p->rl);
+            i = ((u128)__ldcg(&p->ih) << 64) | __ldcg(&p->il);
+            s1 = __ldcg(&p->sr);
+            s2 = __ldcg(&p->si);
+            side = __ldcg(&p->side);
+        }
+        r = warp_sum_u128(r);
+        i = warp_sum_u128(i);
+        const int any = __syncthreads_or(side);
+        if (any) {
+            s1 = warp_sum(s1);
+            s2 = warp_sum(s2);
+        }
+        if (lane == 0) {
+            wint[warp][0] = (unsigned long long)r;
+            wint[warp][1] = (unsigned long long)(r >> 64);
+            wint[warp][2] = (unsigned long long)i;
+            wint[warp][3] = (unsigned long long)(i >> 64);
+            wside[warp][0] = s1;
+            wside[warp][1] = s2;
+            wflag[warp] = 0;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            I192 xr{0, 0, 0}, xi{0, 0, 0};
+            double y1 = 0.0, y2 = 0.0;
+            if (lane < kRgWarps) {
+                xr = i192_from(((u128)wint[lane][1] << 64) | wint[lane][0]);
+                xi = i192_from(((u128)wint[lane][3] << 64) | wint[lane][2]);
+                y1 = wside[lane][0];
+                y2 = wside[lane][1];
+            }
+            xr = warp_sum_i192(xr);
+            xi = warp_sum_i192(xi);
+            if (any) {
+                y1 = warp_sum(y1);
+                y2 = warp_sum(y2);
+            }
+            if (lane == 0) {
+                const double mr = (i192_to_double(xr) * 0x1p-100 + y1) * a.inv_n;
+                const double mi = (i192_to_double(xi) * 0x1p-100 + y2) * a.inv_n;
+                const double tr = 2.0 * mr, ti = 2.0 * mi;
+                const float hr = (float)tr, hi = (float)ti;
+                s_mu.mu = make_double2(mr, mi);
+                s_mu.two = make_double2(tr, ti);
+                s_mu.two32 = make_float4(hr, (float)(tr - (double)hr), hi, (float)(ti - (double)hi));
+            }
+        }
+        __syncthreads();
+    }
+    for (uint32_t j = threadIdx.x; j < nv; j += kRgThreads) g[j] = sl[j];
+    if (rank == 0 && threadIdx.x == 0 && !s_abort) *a.mu_out = s_mu;
+}
+
+template <class T> cudaError_t launch_grid_t(const ResGridArgs &a, unsigned G, size_t smem, cudaStream_t st) {
+    auto kern = k_resident_grid<T>;
+    static size_t smem_set = 0;
+    cudaError_t e;
+    if (smem > smem_set) {
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+            return e;
+        smem_set = smem;
+    }
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRgThreads, smem)) != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorNotSupported;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(G);
+    cfg.blockDim = dim3(kRgThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;  // all G CTAs co-resident, or the launch fails
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
 template <class T> cudaError_t launch_cluster_t(const ResArgs &a, unsigned C, size_t smem, cudaStream_t st) {
     auto kern = k_resident_cluster<T>;
     static size_t smem_set = 0;
@@ -301,6 +579,28 @@ bool resident_plan(int n, grover_dtype dt, unsigned *C_out, uint32_t *slice_vecs
         return true;
     }
     return false;
+}
+
+// Grid-wide variant: one CTA per SM; the slices (and their marked bitmasks)
+// must fit one CTA's shared memory.
+bool resident_grid_plan(int n, grover_dtype dt, int sm_count, unsigned *G_out, uint32_t *slice_vecs,
+                        size_t *smem_out) {
+    const uint64_t N = 1ull << n;
+    const int apv = dt == GROVER_C64 ? 2 : 1;
+    const uint64_t nvec = N / apv;
+    if (sm_count < 1 || sm_count > kRgThreads || nvec < (uint64_t)sm_count) return false;
+    const uint64_t L = (nvec + sm_count - 1) / sm_count;
+    const size_t smem = (size_t)L * 16 + ((L * apv + 31) / 32) * 4;
+    if (smem > kRgSmemMax) return false;
+    *G_out = (unsigned)((nvec + L - 1) / L);
+    *slice_vecs = (uint32_t)L;
+    *smem_out = smem;
+    return true;
+}
+
+cudaError_t launch_resident_grid(const ResGridArgs &a, grover_dtype dt, unsigned G, size_t smem, cudaStream_t st) {
+    if (dt == GROVER_C64) return launch_grid_t<float>(a, G, smem, st);
+    return launch_grid_t<double>(a, G, smem, st);
 }
 
 cudaError_t launch_resident(const ResArgs &a, grover_dtype dt, unsigned C, size_t smem, cudaStream_t st) {

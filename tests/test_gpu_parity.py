@@ -319,12 +319,13 @@ def test_resident_forced(B, dtype, n):
 
 
 def test_resident_refuses_large_states(B):
-    st = B.State(19, "c64")
-    st.set_resident(1)
-    st.init_uniform()
-    with pytest.raises(B.GroverError) as ei:
-        st.iterate(B.Marked(19, [3]), 2)
-    assert ei.value.status == 8  # GROVER_EUNSUPPORTED
+    for opt in (1, 2):
+        st = B.State(23, "c64")
+        st.set_resident(opt)
+        st.init_uniform()
+        with pytest.raises(B.GroverError) as ei:
+            st.iterate(B.Marked(23, [3]), 2)
+        assert ei.value.status == 8  # GROVER_EUNSUPPORTED
     st2 = B.State(10, "c64")
     st2.set_resident(1)
     st2.set_accum("kahan")
@@ -344,3 +345,82 @@ def test_resident_deterministic_and_equal_groups(B):
         outs.append(to_np(st))
     assert np.array_equal(outs[0], outs[1])
     check_groups(outs[0], marked)
+
+
+# ---- grid-wide persistent iterator ---------------------------------------------------------
+@pytest.mark.parametrize("dtype,n", [("c64", 9), ("c64", 12), ("c64", 18), ("c64", 21), ("c64", 22), ("c128", 10),
+                                     ("c128", 16), ("c128", 21)])
+def test_resident_grid_forced(B, dtype, n):
+    """The grid iterator (forced) against the oracle from a Gaussian start,
+    with a marked list and a bitmask, then continued by the pass path."""
+    m = min(7, 1 << n)
+    marked = inputs.marked_indices(n, m, seed=170 + n)
+    psi0 = inputs.gaussian_state(n, seed=171 + n)
+    if dtype == "c64":
+        psi0 = psi0.astype(np.complex64).astype(np.complex128)
+    k1, k2 = (23, 9) if n <= 18 else (5, 3)
+    ref1 = oracle.grover_operator(psi0.copy(), n, marked, k1)
+    ref2 = oracle.grover_operator(ref1.copy(), n, marked, k2)
+    tol = (lambda k: 1e-12) if dtype == "c128" else c64_tol
+    marks = [B.Marked(n, marked)]
+    if n <= 18:
+        marks.append(B.Marked(n, bitmask=inputs.bitmask(n, marked)))
+    for mk in marks:
+        st = B.State(n, dtype)
+        st.set_resident(2)
+        st.init_state(psi0)
+        st.iterate(mk, k1)
+        st.sync()
+        assert np.max(np.abs(to_np(st) - ref1)) <= tol(k1)
+        st.set_resident(0)
+        st.iterate(mk, k2)
+        assert np.max(np.abs(to_np(st) - ref2)) <= tol(k1 + k2)
+
+
+@pytest.mark.parametrize("dtype,n,m", [("c64", 20, 1), ("c64", 22, 4), ("c128", 19, 2)])
+def test_resident_grid_full_run_uniform(B, dtype, n, m):
+    """Full optimal run from the uniform state on the grid iterator: closed
+    form, bitwise-equal groups, and the same result on a second run."""
+    marked = inputs.marked_indices(n, m, seed=180 + n)
+    k = B.grover_optimal_iterations(n, m)
+    outs = []
+    for _ in range(2):
+        st = B.State(n, dtype)
+        st.set_resident(2)
+        st.init_uniform()
+        st.iterate(B.Marked(n, marked), k)
+        st.sync()
+        outs.append(to_np(st))
+    assert np.array_equal(outs[0], outs[1])
+    check_groups(outs[0], marked)
+    a_m, a_u = oracle.closed_form_uniform(n, m, k)
+    tol = 1e-11 if dtype == "c128" else 3 * k * 2.0 ** -24
+    idx = marked.astype(np.int64)
+    assert abs(outs[0][idx[0]] - a_m) <= tol
+    other = 0 if idx[0] != 0 else 1
+    assert abs(outs[0][other] - a_u) <= tol
+
+
+def test_resident_grid_wait_runs_out(B):
+    """Failure detection without a GPU fault: CTA 0 withholds its first partial
+    (test hook), every CTA's bounded wait runs out, the kernel returns and
+    grover_sync reports GROVER_ETIMEOUT; the handle stays usable."""
+    n = 18
+    marked = inputs.marked_indices(n, 2, seed=190)
+    st = B.State(n, "c64")
+    mk = B.Marked(n, marked)
+    st.set_resident(2)
+    st.set_option(2, 20000)  # wait limit: 20000 polls
+    st.set_option(3, 1)      # stall hook
+    st.init_uniform()
+    st.iterate(mk, 10)
+    with pytest.raises(B.GroverError) as ei:
+        st.sync()
+    assert ei.value.status == 4  # GROVER_ETIMEOUT
+    st.set_option(2, 1 << 22)
+    st.init_uniform()
+    k = B.grover_optimal_iterations(n, 2)
+    st.iterate(mk, k)
+    st.sync()
+    a_m, _ = oracle.closed_form_uniform(n, 2, k)
+    assert abs(to_np(st)[int(marked[0])] - a_m) <= 3 * k * 2.0 ** -24
