@@ -111,13 +111,13 @@ typedef enum {
      *            complex64, n <= 17 complex128), partials exchanged through
      *            distributed shared memory;
      *   grid:    one CTA per SM (cooperative launch; 152 x 226 KiB on GB300:
-     *            n <= 22 complex64, n <= 21 complex128), partials exchanged
-     *            through tagged global slots with bounded waits (a wait that
-     *            runs out sets the status word: GROVER_ETIMEOUT at
-     *            grover_sync).
-     *   -1 (default): the cluster iterator for n <= 17 (complex64) or n <= 15
-     *                 (complex128); the grid iterator for 19 <= n <= 22
-     *                 (complex64) or 18 <= n <= 20 (complex128); else one
+     *            n <= 22 complex64, n <= 21 complex128), partials added as
+     *            integer limbs into global accumulators, an arrival counter
+     *            with bounded waits (a wait that runs out sets the status
+     *            word: GROVER_ETIMEOUT at grover_sync).
+     *   -1 (default): the cluster iterator for n <= 16 (complex64) or n <= 14
+     *                 (complex128); the grid iterator for 17 <= n <= 22
+     *                 (complex64) or 15 <= n <= 21 (complex128); else one
      *                 fused pass per iteration (the faster choice at each n
      *                 as measured on GB300);
      *    0: always one fused pass per iteration;

@@ -415,10 +415,11 @@ grover_status grover_iterate(grover_state *s, const grover_marked *mk, uint64_t 
         const bool grid_fits = exact_ok && resident_grid_plan(s->n, s->dtype, s->geo.sm_count, &G, &gv, &gsmem);
         // automatic choice, from per-iteration times measured on GB300: one
         // cluster up to cluster_max; the whole grid for [grid_min, grid_max]
-        // (its exchange through global memory costs about 5.5 us per
-        // iteration, so it wins only once a pass costs more); passes otherwise
+        // (its exchange through global memory costs about 3.3 us per
+        // iteration, against 2.7 us for the cluster's at small n); passes
+        // otherwise
         const bool c64 = s->dtype == GROVER_C64;
-        const int cluster_max = c64 ? 17 : 15, grid_min = c64 ? 19 : 18, grid_max = c64 ? 22 : 20;
+        const int cluster_max = c64 ? 16 : 14, grid_min = c64 ? 17 : 15, grid_max = c64 ? 22 : 21;
         const bool use_cluster = cluster_fits && (s->resident == 1 || (s->resident == -1 && s->n <= cluster_max));
         const bool use_grid = !use_cluster && grid_fits &&
                               (s->resident >= 1 || (s->resident == -1 && s->n >= grid_min && s->n <= grid_max));
@@ -439,8 +440,7 @@ grover_status grover_iterate(grover_state *s, const grover_marked *mk, uint64_t 
             (void)cudaGetLastError();
             if (s->resident == 1) return cuda_fail(s, e, "persistent iterator launch");
         } else if (use_grid) {
-            const size_t slot_bytes = sizeof(GridSlot) * 2 * 512;
-            if (!s->rg_mem) CK(s, cudaMalloc(&s->rg_mem, slot_bytes + 256), "cudaMalloc(grid iterator slots)");
+            if (!s->rg_mem) CK(s, cudaMalloc(&s->rg_mem, kRgBytes), "cudaMalloc(grid iterator region)");
             ResGridArgs r;
             r.amps = s->amps;
             r.nvec = nvec_of(s);
@@ -449,13 +449,14 @@ grover_status grover_iterate(grover_state *s, const grover_marked *mk, uint64_t 
             r.k = k;
             r.inv_n = ldexp(1.0, -s->n);
             r.mu_out = s->sc.mu + s->mu_slot;
-            r.slots = (GridSlot *)s->rg_mem;
-            r.counter = (unsigned long long *)((char *)s->rg_mem + slot_bytes);
+            r.acc = (unsigned long long *)s->rg_mem;
+            r.counter = r.acc + (size_t)2 * kRgWords * kRgLine;
+            r.side = (double2 *)((char *)s->rg_mem + kRgAccBytes);
             r.status = s->sc.status;
             r.wait_limit = s->wait_limit;
             r.stall = s->test_stall;
             s->test_stall = 0;
-            CK(s, cudaMemsetAsync(r.counter, 0, sizeof(unsigned long long), s->stream), "grid iterator counter reset");
+            CK(s, cudaMemsetAsync(s->rg_mem, 0, kRgAccBytes, s->stream), "grid iterator reset");
             cudaError_t e = launch_resident_grid(r, s->dtype, G, gsmem, s->stream);
             if (e == cudaSuccess) {
                 s->mu_valid = true;

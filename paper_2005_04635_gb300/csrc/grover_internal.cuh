@@ -120,14 +120,15 @@ struct ResArgs {
 bool resident_plan(int n, grover_dtype dt, unsigned *C, uint32_t *slice_vecs, size_t *smem);
 cudaError_t launch_resident(const ResArgs &a, grover_dtype dt, unsigned C, size_t smem, cudaStream_t st);
 // Grid-wide variant (cooperative launch, one CTA per SM, partials exchanged
-// through global slots and an arrival counter).
+// through limb accumulators and an arrival counter in global memory).
 constexpr size_t kRgSmemMax = 226 * 1024;  // dynamic shared memory per CTA
-struct GridSlot {
-    unsigned long long rl, rh, il, ih;  // exact partial (128-bit Re, Im)
-    double sr, si;                      // FP64 side sums
-    int side;
-    int pad;
-};
+constexpr int kRgWords = 7;                // 3 + 3 limbs and a side-sum count per parity
+constexpr int kRgLine = 16;                // 64-bit words per 128-byte line
+constexpr int kRgMaxGrid = 512;
+// Layout of the handle's grid-iterator region (zeroed before every launch):
+// accumulators [2][kRgWords] lines, counter line, side sums [2][kRgMaxGrid].
+constexpr size_t kRgAccBytes = sizeof(unsigned long long) * kRgLine * (2 * kRgWords + 1);
+constexpr size_t kRgBytes = kRgAccBytes + sizeof(double2) * 2 * kRgMaxGrid;
 struct ResGridArgs {
     void *amps;
     uint64_t nvec;          // 16-byte vectors in the state
@@ -136,8 +137,9 @@ struct ResGridArgs {
     uint64_t k;
     double inv_n;
     MeanSlot *mu_out;
-    GridSlot *slots;        // [2][grid]
-    unsigned long long *counter;  // arrivals, zeroed before the launch
+    unsigned long long *acc;      // [2][kRgWords] accumulators, kRgLine apart
+    unsigned long long *counter;  // arrivals
+    double2 *side;          // [2][grid] FP64 side sums
     int *status;            // set to 3 if a wait runs out
     long long wait_limit;   // polls of the counter before giving up
     int stall;              // test hook: CTA 0 never reports its first partial
@@ -250,7 +252,7 @@ struct grover_state {
     bool mu_valid;          // cached mean of flip_key(c) is valid
     uint64_t mu_key;        // 0: mean of c itself; else id of the marked set applied
     void *phase_mem;        // phase-iterator scratch (allocated on first use)
-    void *rg_mem;           // grid-resident iterator slots + counter (allocated on first use)
+    void *rg_mem;           // grid-resident iterator accumulators, counter, side sums (first use)
     char err[512];
 };
 

@@ -251,20 +251,29 @@ __global__ void __launch_bounds__(kResThreads) k_resident_cluster(ResArgs a) {
 // ---- grid-wide variant ----------------------------------------------------------------
 // The same iteration over all SMs: a cooperative launch of G CTAs (one per SM,
 // all co-resident), CTA r keeping vectors [r*L, min((r+1)*L, nvec)) in shared
-// memory.  There is no hardware barrier across the grid, so the partials are
-// exchanged through global memory: each CTA writes its exact partial to its
-// slot and adds 1 to a counter with release semantics; one thread per CTA
-// polls the counter (acquire loads, at most wait_limit polls) until all G
-// partials of the iteration are in (the counter was zeroed before the launch
-// and only grows: G * (t + 2) after iteration t), then threads 0..G-1 read
-// the G slots and the CTA adds them in rank order -- the bitwise identical
-// mean in every CTA.  Slots are double buffered by iteration parity: a CTA
-// writes a slot again only after the counter shows every CTA's next partial,
-// which each CTA adds only after it has read the slot.  A wait that runs out
-// sets *status = 3 and the CTA leaves the loop (the others then run out too).
+// memory.  There is no hardware barrier across the grid, so the partials meet
+// in global memory: each CTA adds its exact 128-bit partials, split into
+// 43-bit limbs, into six 64-bit accumulators (integer adds: exact and
+// independent of the order), then adds 1 to an arrival counter with release
+// semantics.  One thread per CTA polls the counter with acquire loads (at most
+// wait_limit polls; the counter was zeroed before the launch and reads
+// G * (t + 2) once iteration t is in), reads the six accumulators and
+// rebuilds the total, so every CTA holds the bitwise identical mean.  Each
+// accumulator has its own 128-byte line (the adds of different words do not
+// queue behind one another).  Accumulators are double buffered by iteration
+// parity and never reset within a launch: a CTA takes the difference from
+// what it read two iterations earlier.  A CTA adds into a parity set again
+// only after the counter shows every CTA's next partial, which each CTA adds
+// only after it has read the set.  FP64 side sums (values outside the fixed-
+// point window) go to per-CTA slots, added in rank order when a seventh
+// accumulator shows that some CTA had any.  A wait that runs out sets
+// *status = 3 and the CTA leaves the loop (the others then run out too).
 constexpr int kRgThreads = 512;
 constexpr int kRgWarps = kRgThreads / 32;
 
+__device__ __forceinline__ void red_add_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
 __device__ __forceinline__ void red_release_add_u64(unsigned long long *p, unsigned long long v) {
     asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
@@ -291,7 +300,7 @@ __global__ void __launch_bounds__(kRgThreads, 1) k_resident_grid(ResGridArgs a) 
     uint32_t *fm = reinterpret_cast<uint32_t *>(smem + (size_t)a.slice_vecs * sizeof(V));
     __shared__ unsigned long long wint[kRgWarps][4];
     __shared__ double wside[kRgWarps][2];
-    __shared__ int wflag[kRgWarps];
+    __shared__ unsigned long long s_prev[2][kRgWords];
     __shared__ MeanSlot s_mu;
     __shared__ int s_abort;
 
@@ -300,6 +309,7 @@ __global__ void __launch_bounds__(kRgThreads, 1) k_resident_grid(ResGridArgs a) 
     for (uint32_t j = threadIdx.x; j < nv; j += kRgThreads) sl[j] = g[j];
     for (uint32_t w = threadIdx.x; w < nwords; w += kRgThreads) fm[w] = 0u;
     if (threadIdx.x == 0) s_abort = 0;
+    if (threadIdx.x < 2 * kRgWords) s_prev[threadIdx.x / kRgWords][threadIdx.x % kRgWords] = 0ull;
     __syncthreads();
     if (a.mk.mode == MARK_LIST) {
         for (uint64_t i = threadIdx.x; i < a.mk.m; i += kRgThreads) {
@@ -412,15 +422,25 @@ __global__ void __launch_bounds__(kRgThreads, 1) k_resident_grid(ResGridArgs a) 
             }
             const bool withhold = a.stall && t == -1 && rank == 0;  // test hook: this partial never arrives
             if (lane == 0) {
-                GridSlot *p = a.slots + (size_t)par * G + rank;
-                p->rl = (unsigned long long)r;
-                p->rh = (unsigned long long)(r >> 64);
-                p->il = (unsigned long long)i;
-                p->ih = (unsigned long long)(i >> 64);
-                p->sr = s1;
-                p->si = s2;
-                p->side = any_side;
-                if (!withhold) red_release_add_u64(a.counter, 1ull);
+                unsigned long long *acc = a.acc + (size_t)par * kRgWords * kRgLine;
+                if (!withhold) {
+                    // 43-bit limbs of the two's complement partials: 152 of them
+                    // sum to less than 2^51, so the 64-bit adds cannot carry out
+                    const u128 lm = ((u128)1 << 43) - 1;
+                    red_add_u64(acc + 0 * kRgLine, (unsigned long long)(r & lm));
+                    red_add_u64(acc + 1 * kRgLine, (unsigned long long)((r >> 43) & lm));
+                    red_add_u64(acc + 2 * kRgLine, (unsigned long long)(r >> 86));
+                    red_add_u64(acc + 3 * kRgLine, (unsigned long long)(i & lm));
+                    red_add_u64(acc + 4 * kRgLine, (unsigned long long)((i >> 43) & lm));
+                    red_add_u64(acc + 5 * kRgLine, (unsigned long long)(i >> 86));
+                    if (any_side) {
+                        a.side[(size_t)par * G + rank] = make_double2(s1, s2);
+                        red_add_u64(acc + 6 * kRgLine, 1ull);
+                    } else {
+                        a.side[(size_t)par * G + rank] = make_double2(0.0, 0.0);
+                    }
+                    red_release_add_u64(a.counter, 1ull);
+                }
                 // wait until the G partials of this iteration are in
                 const unsigned long long target = (unsigned long long)G * (unsigned long long)(t + 2);
                 long long polls = 0;
@@ -432,6 +452,34 @@ __global__ void __launch_bounds__(kRgThreads, 1) k_resident_grid(ResGridArgs a) 
                     }
                 }
                 s_abort = to;
+                if (!to) {
+                    // this iteration's totals: the accumulators minus what they held
+                    // two iterations ago (same parity)
+                    unsigned long long d[kRgWords];
+#pragma unroll
+                    for (int w = 0; w < kRgWords; ++w) {
+                        const unsigned long long v = __ldcg(acc + w * kRgLine);
+                        d[w] = v - s_prev[par][w];
+                        s_prev[par][w] = v;
+                    }
+                    const u128 R = (u128)d[0] + ((u128)d[1] << 43) + ((u128)d[2] << 86);
+                    const u128 I = (u128)d[3] + ((u128)d[4] << 43) + ((u128)d[5] << 86);
+                    double y1 = 0.0, y2 = 0.0;
+                    if (d[6]) {  // some CTA had out-of-window values: add its side sums in rank order
+                        for (unsigned q = 0; q < G; ++q) {
+                            const double2 v = __ldcg(a.side + (size_t)par * G + q);
+                            y1 += v.x;
+                            y2 += v.y;
+                        }
+                    }
+                    const double mr = (i192_to_double(i192_from(R)) * 0x1p-100 + y1) * a.inv_n;
+                    const double mi = (i192_to_double(i192_from(I)) * 0x1p-100 + y2) * a.inv_n;
+                    const double tr = 2.0 * mr, ti = 2.0 * mi;
+                    const float hr = (float)tr, hi = (float)ti;
+                    s_mu.mu = make_double2(mr, mi);
+                    s_mu.two = make_double2(tr, ti);
+                    s_mu.two32 = make_float4(hr, (float)(tr - (double)hr), hi, (float)(ti - (double)hi));
+                }
             }
         }
         __syncthreads();
@@ -439,61 +487,6 @@ __global__ void __launch_bounds__(kRgThreads, 1) k_resident_grid(ResGridArgs a) 
             if (threadIdx.x == 0) atomicExch(a.status, 3);
             break;
         }
-        // gather: thread q < G reads CTA q's partial
-        u128 r = 0, i = 0;
-        double s1 = 0.0, s2 = 0.0;
-        int side = 0;
-        if (threadIdx.x < G) {
-            const GridSlot *p = a.slots + (size_t)par * G + threadIdx.x;
-            r = ((u128)__ldcg(&p->rh) << 64) | __ldcg(&p->rl);
-            i = ((u128)__ldcg(&p->ih) << 64) | __ldcg(&p->il);
-            s1 = __ldcg(&p->sr);
-            s2 = __ldcg(&p->si);
-            side = __ldcg(&p->side);
-        }
-        r = warp_sum_u128(r);
-        i = warp_sum_u128(i);
-        const int any = __syncthreads_or(side);
-        if (any) {
-            s1 = warp_sum(s1);
-            s2 = warp_sum(s2);
-        }
-        if (lane == 0) {
-            wint[warp][0] = (unsigned long long)r;
-            wint[warp][1] = (unsigned long long)(r >> 64);
-            wint[warp][2] = (unsigned long long)i;
-            wint[warp][3] = (unsigned long long)(i >> 64);
-            wside[warp][0] = s1;
-            wside[warp][1] = s2;
-            wflag[warp] = 0;
-        }
-        __syncthreads();
-        if (warp == 0) {
-            I192 xr{0, 0, 0}, xi{0, 0, 0};
-            double y1 = 0.0, y2 = 0.0;
-            if (lane < kRgWarps) {
-                xr = i192_from(((u128)wint[lane][1] << 64) | wint[lane][0]);
-                xi = i192_from(((u128)wint[lane][3] << 64) | wint[lane][2]);
-                y1 = wside[lane][0];
-                y2 = wside[lane][1];
-            }
-            xr = warp_sum_i192(xr);
-            xi = warp_sum_i192(xi);
-            if (any) {
-                y1 = warp_sum(y1);
-                y2 = warp_sum(y2);
-            }
-            if (lane == 0) {
-                const double mr = (i192_to_double(xr) * 0x1p-100 + y1) * a.inv_n;
-                const double mi = (i192_to_double(xi) * 0x1p-100 + y2) * a.inv_n;
-                const double tr = 2.0 * mr, ti = 2.0 * mi;
-                const float hr = (float)tr, hi = (float)ti;
-                s_mu.mu = make_double2(mr, mi);
-                s_mu.two = make_double2(tr, ti);
-                s_mu.two32 = make_float4(hr, (float)(tr - (double)hr), hi, (float)(ti - (double)hi));
-            }
-        }
-        __syncthreads();
     }
     for (uint32_t j = threadIdx.x; j < nv; j += kRgThreads) g[j] = sl[j];
     if (rank == 0 && threadIdx.x == 0 && !s_abort) *a.mu_out = s_mu;
