@@ -20,8 +20,8 @@
 // four bulk copies for a contiguous lowest-group tile; mbarrier transaction
 // count) while the current tile is multiplied and stored.  Operands live in shared memory in
 // the no-swizzle K-major layout (8 x 16-byte core matrices; leading byte
-// offset = 128 B between core matrices along K, stride byte offset = 8-row
-// group stride); one thread issues 3 x K/16 tcgen05.mma (M = 128, N = K or
+// offset = 144 B between core matrices along K, stride byte offset = 8-row
+// group stride, both padded against bank conflicts); one thread issues 3 x K/16 tcgen05.mma (M = 128, N = K or
 // 128, K = 16 each) and a tcgen05.commit to an mbarrier; the epilogue reads
 // the accumulators with tcgen05.ld, applies the pass scale (exact power of
 // two) and the phase shift 2|0><0| - I where asked, and stores.  Every
@@ -58,9 +58,20 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
-// byte offset of element (row, k) in a K-major no-swizzle bf16 operand with K columns
+// Padded no-swizzle K-major operand layout.  A core matrix (8 rows x 8 bf16
+// along K) is 128 contiguous bytes; core matrices adjacent along K are LBO =
+// 144 bytes apart and 8-row groups SBO bytes apart, SBO = 18 K rounded up to
+// 16 (mod 128).  The 16-byte pads put the eight k-groups of one row, and the
+// rows 4c..4c+3 of eight consecutive c, on distinct bank groups, so the
+// slice stores below are free of shared-memory bank conflicts (unpadded, the
+// k-groups of a row were all 128 bytes apart, on the same banks).
+constexpr uint32_t kLBO = 144;
+__host__ __device__ constexpr uint32_t sbo_of(int K) {
+    return 18u * (uint32_t)K + ((16u - ((18u * (uint32_t)K) & 127u)) & 127u);
+}
+// byte offset of element (row, k) in that layout for a K-column operand
 __device__ __forceinline__ uint32_t kmaj_off(int row, int k, int K) {
-    return (uint32_t)((row >> 3) * ((K >> 3) * 128) + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+    return (uint32_t)((row >> 3) * sbo_of(K) + (k >> 3) * kLBO + (row & 7) * 16 + (k & 7) * 2);
 }
 
 __device__ __forceinline__ void split3(float x, float &b0, float &b1, float &b2) {
@@ -164,9 +175,9 @@ k_wht_tc(float *amps, const __grid_constant__ CUtensorMap tmap, int lo, uint64_t
          int negate_but_zero, int *status, long long wait_limit, int stall) {
     constexpr int K = 1 << KB;
     constexpr size_t STAGE = (size_t)K * (kCols / 2) * 8;  // fp32 tile
-    constexpr size_t SLICE = (size_t)kCols * K * 2;        // one bf16 slice of the tile
-    constexpr uint32_t SBO = (K / 8) * 128;
-    constexpr uint32_t LBO = 128;
+    constexpr uint32_t SBO = sbo_of(K);
+    constexpr uint32_t LBO = kLBO;
+    constexpr size_t SLICE = (size_t)(kCols / 8) * SBO;    // one bf16 slice of the tile (128 rows)
     constexpr int M_MMA = 128;
     constexpr int N_MMA = LOW ? kCols : K;
     static_assert(!LOW || KB == 7, "the lowest group uses W as the 128-row operand");
@@ -388,7 +399,8 @@ template <int KB, bool LOW>
 cudaError_t launch_tc_t(void *amps, int n, int lo, float scale, bool negate, int *status, long long wait_limit,
                         int stall, cudaStream_t st, const Geometry &g) {
     constexpr int K = 1 << KB;
-    const size_t smem = (size_t)K * (kCols / 2) * 8 + 3 * (size_t)kCols * K * 2 + (size_t)K * K * 2;
+    // fp32 stage, three bf16 slices (128 rows), W (K rows), padded layout
+    const size_t smem = (size_t)K * (kCols / 2) * 8 + 3 * (size_t)(kCols / 8) * sbo_of(K) + (size_t)(K / 8) * sbo_of(K);
     auto kern = k_wht_tc<KB, LOW>;
     static bool attr = false;
     if (!attr) {
