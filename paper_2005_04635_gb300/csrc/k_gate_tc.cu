@@ -12,9 +12,13 @@
 //     amplitudes (column = (block, re/im)); D = W X, so TMEM lane = output mid
 //     and each thread stores (re, im) pairs, 256 contiguous bytes per warp.
 // W is exact in bf16.  Each FP32 amplitude is split into three bf16 slices
-// x = b0 + b1 + b2 (each the round-to-nearest of the remainder); each slice
-// product has its own FP32 accumulator in tensor memory, and the epilogue adds
-// them smallest first with round to nearest.
+// x = b0 + b1 + b2 (each the round-to-nearest of the remainder).  The b0
+// products accumulate in one FP32 tensor-memory accumulator (A0), the b1 and b2
+// products in a second (A12, about 2^-8 of A0, so the accumulator's own
+// rounding there is below 2^-32 of the result instead of biasing the large
+// one); the epilogue adds A12 + A0 with round to nearest.  Two such pairs
+// (512 TMEM columns) alternate between tiles, so the epilogue of one tile
+// runs while the tensor cores multiply the next.
 // Pipeline per CTA (one per SM): the next tile streams into an fp32 staging
 // buffer by TMA (one tiled cp.async.bulk.tensor copy per upper-group tile,
 // four bulk copies for a contiguous lowest-group tile; mbarrier transaction
@@ -224,8 +228,65 @@ k_wht_tc(float *amps, const __grid_constant__ CUtensorMap tmap, int lo, uint64_t
     bool load_pending = blockIdx.x < ntiles, mma_pending = false;
     if (warp == 0 && load_pending) issue_tile_load<KB, LOW>(amps, &tmap, blockIdx.x, lo, stage, &tma_bar, lane);
 
-    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const uint64_t abase = tile_base<KB, LOW>(tile, lo);
+    // Epilogue of a finished tile from TMEM buffer `buf`: A12 + A0 (one
+    // rounding), scale, phase shift, store.
+    auto epilogue = [&](uint64_t etile, uint32_t buf) {
+        const uint64_t abase = tile_base<KB, LOW>(etile, lo);
+        const int lg = warp & 3, cg = warp >> 2;
+        constexpr int NCH = N_MMA / 32;
+        if (cg < NCH) {
+            uint32_t a[32], b[32];
+            const uint32_t t0 = taddr + 256u * buf + ((uint32_t)(32 * lg) << 16) + (uint32_t)(32 * cg);
+            tmem_ld32(t0 + 128u, a);
+            tmem_ld32(t0, b);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) a[j] = __float_as_uint(__uint_as_float(a[j]) + __uint_as_float(b[j]));
+            const int row = 32 * lg + lane;
+            if (LOW) {
+                // row = output mid, registers = 16 blocks x (re, im)
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const uint64_t a0 = abase + (uint64_t)(16 * cg + q) * K + row;
+                    float re = __uint_as_float(a[2 * q]) * scale, im = __uint_as_float(a[2 * q + 1]) * scale;
+                    if (negate_but_zero && a0 != 0) {
+                        re = -re;
+                        im = -im;
+                    }
+                    __stcs(reinterpret_cast<float2 *>(amps) + a0, make_float2(re, im));
+                }
+            } else {
+                // row = column (re or im of amplitude row / 2), registers = output
+                // mids; lanes 2l and 2l + 1 hold re and im of one amplitude: they
+                // swap halves so each stores (re, im) pairs for 16 mids
+                const uint64_t ar = abase + (uint64_t)(row >> 1);
+                const bool odd = lane & 1;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    // even lane keeps mid 2j (its re) and receives the im of mid 2j;
+                    // odd lane keeps mid 2j + 1 (its im) and receives the re of mid 2j + 1
+                    const float mine_e = __uint_as_float(a[2 * j]), mine_o = __uint_as_float(a[2 * j + 1]);
+                    const float give = odd ? mine_e : mine_o;
+                    const float got = __shfl_xor_sync(0xffffffffu, give, 1);
+                    const int mid = 32 * cg + 2 * j + (odd ? 1 : 0);
+                    const uint64_t a0 = ar + ((uint64_t)mid << lo);
+                    float re = (odd ? got : mine_e) * scale, im = (odd ? mine_o : got) * scale;
+                    if (negate_but_zero && a0 != 0) {
+                        re = -re;
+                        im = -im;
+                    }
+                    __stcs(reinterpret_cast<float2 *>(amps) + a0, make_float2(re, im));
+                }
+            }
+        }
+    };
+
+    // Per tile i: build the slices of tile i; issue the load of tile i + 1 and
+    // the MMAs of tile i into TMEM buffer i & 1; while they run, the epilogue
+    // of tile i - 1 drains buffer (i - 1) & 1; then wait for the MMAs (the
+    // slices are free again).
+    uint64_t prev = ~0ull;
+    uint32_t it = 0;
+    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
         // ---- staged fp32 tile -> three bf16 slices ----
         if (!mbar_wait(&tma_bar, loads_done & 1, wait_limit)) {
             atomicExch(status, 2);
@@ -273,13 +334,14 @@ k_wht_tc(float *amps, const __grid_constant__ CUtensorMap tmap, int lo, uint64_t
         fence_before();
         __syncthreads();
         fence_after();
-        // ---- next tile's load overlaps this tile's MMAs and epilogue ----
+        // ---- next tile's load ----
         const uint64_t next = tile + gridDim.x;
         if (warp == 0 && next < ntiles) issue_tile_load<KB, LOW>(amps, &tmap, next, lo, stage, &tma_bar, lane);
         load_pending = next < ntiles;
-        // ---- MMA: one accumulator per slice (TMEM columns 128 s .. 128 s + N) ----
+        // ---- MMA into buffer it & 1: A0 = W b0 (or b0 W), A12 = W (b1 + b2) ----
         if (tid == 0) {
             constexpr uint32_t idesc = idesc_bf16(M_MMA, N_MMA);
+            const uint32_t tb = taddr + 256u * (it & 1u);
 #pragma unroll 1
             for (int s = 0; s < 3; ++s) {
 #pragma unroll 1
@@ -288,10 +350,10 @@ k_wht_tc(float *amps, const __grid_constant__ CUtensorMap tmap, int lo, uint64_t
                     const uint32_t wa = su32(ws) + kk * 2 * LBO;
                     const uint64_t da = LOW ? smem_desc(wa, LBO, SBO) : smem_desc(xa, LBO, SBO);
                     const uint64_t db = LOW ? smem_desc(xa, LBO, SBO) : smem_desc(wa, LBO, SBO);
-                    const uint32_t acc = kk != 0;
+                    const uint32_t acc = (s == 2) || kk != 0;
                     asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-                                 ::"r"(taddr + 128u * s), "l"(da), "l"(db), "r"(idesc), "r"(acc) : "memory");
+                                 ::"r"(tb + (s ? 128u : 0u)), "l"(da), "l"(db), "r"(idesc), "r"(acc) : "memory");
                 }
             }
             // test hook: without the commit nothing arrives on mma_bar
@@ -300,58 +362,24 @@ k_wht_tc(float *amps, const __grid_constant__ CUtensorMap tmap, int lo, uint64_t
                              ::"r"(su32(&mma_bar)) : "memory");
         }
         mma_pending = true;
+        // ---- epilogue of the previous tile, overlapping the MMAs ----
+        if (prev != ~0ull) epilogue(prev, (it - 1) & 1u);
         if (!mbar_wait(&mma_bar, mmas_done & 1, wait_limit)) {
             atomicExch(status, 2);
             s_abort = 1;
         }
-        fence_after();
-        __syncthreads();
-        if (s_abort) break;
-        ++mmas_done;
-        mma_pending = false;
-        // ---- epilogue: (acc2 + acc1) + acc0, scale, phase shift, store ----
-        {
-            const int lg = warp & 3, cg = warp >> 2;
-            constexpr int NCH = N_MMA / 32;
-            if (cg < NCH) {
-                uint32_t a[32], b[32];
-                const uint32_t t0 = taddr + ((uint32_t)(32 * lg) << 16) + (uint32_t)(32 * cg);
-                tmem_ld32(t0 + 256u, a);
-                tmem_ld32(t0 + 128u, b);
-#pragma unroll
-                for (int j = 0; j < 32; ++j) a[j] = __float_as_uint(__uint_as_float(a[j]) + __uint_as_float(b[j]));
-                tmem_ld32(t0, b);
-#pragma unroll
-                for (int j = 0; j < 32; ++j) a[j] = __float_as_uint(__uint_as_float(a[j]) + __uint_as_float(b[j]));
-                const int row = 32 * lg + lane;
-                if (LOW) {
-                    // row = output mid, registers = 16 blocks x (re, im)
-#pragma unroll
-                    for (int q = 0; q < 16; ++q) {
-                        const uint64_t a0 = abase + (uint64_t)(16 * cg + q) * K + row;
-                        float re = __uint_as_float(a[2 * q]) * scale, im = __uint_as_float(a[2 * q + 1]) * scale;
-                        if (negate_but_zero && a0 != 0) {
-                            re = -re;
-                            im = -im;
-                        }
-                        __stcs(reinterpret_cast<float2 *>(amps) + a0, make_float2(re, im));
-                    }
-                } else {
-                    // row = column (re or im of amplitude row / 2), registers = output mids
-                    const uint64_t ar = abase + (uint64_t)(row >> 1);
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const uint64_t a0 = ar + ((uint64_t)(32 * cg + j) << lo);
-                        float x = __uint_as_float(a[j]) * scale;
-                        if (negate_but_zero && a0 != 0) x = -x;
-                        __stcs(amps + 2 * a0 + (row & 1), x);
-                    }
-                }
-            }
-        }
         fence_before();
         __syncthreads();
         fence_after();
+        if (s_abort) break;
+        ++mmas_done;
+        mma_pending = false;
+        prev = tile;
+    }
+    if (!s_abort && prev != ~0ull) {
+        epilogue(prev, (it - 1) & 1u);
+        fence_before();
+        __syncthreads();
     }
     // after an abort, wait (bounded) for this CTA's own load and MMA in flight
     // before the tensor memory is freed and the CTA exits
