@@ -577,7 +577,10 @@ grover_status grover_sync(grover_state *s) {
     if (status != 0) {
         CK(s, cudaMemset(s->sc.status, 0, sizeof(int)), "status reset");
         s->mu_valid = false;
-        return fail(s, GROVER_ETIMEOUT, "a bounded device-side wait gave up (status %d)", status);
+        if (status == 4)
+            return fail(s, GROVER_ECUDA, "tensor-core pass skipped: its staging buffer is not 1024-byte aligned");
+        return fail(s, GROVER_ETIMEOUT, "a bounded device-side wait gave up (status %d: %s)", status,
+                    status == 3 ? "grid persistent iterator" : "tensor-core pass");
     }
     return GROVER_OK;
 }

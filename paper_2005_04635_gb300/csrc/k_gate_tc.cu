@@ -20,9 +20,9 @@
 // (512 TMEM columns) alternate between tiles, so the epilogue of one tile
 // runs while the tensor cores multiply the next.
 // Pipeline per CTA (one per SM): the next tile streams into an fp32 staging
-// buffer by TMA (one tiled cp.async.bulk.tensor copy per upper-group tile,
-// four bulk copies for a contiguous lowest-group tile; mbarrier transaction
-// count) while the current tile is multiplied and stored.  Operands live in shared memory in
+// buffer by TMA (one tiled cp.async.bulk.tensor copy per tile; the lowest
+// group's with the 128-byte swizzle so its reads are free of bank conflicts;
+// mbarrier transaction count) while the current tile is multiplied and stored.  Operands live in shared memory in
 // the no-swizzle K-major layout (8 x 16-byte core matrices; leading byte
 // offset = 144 B between core matrices along K, stride byte offset = 8-row
 // group stride, both padded against bank conflicts); one thread issues 3 x K/16 tcgen05.mma (M = 128, N = K or
@@ -154,11 +154,14 @@ __device__ __forceinline__ void issue_tile_load(const float *amps, const CUtenso
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(TILEB) : "memory");
     __syncwarp();
     if (LOW) {
-        constexpr uint32_t PART = TILEB / 4;
-        if (lane < 4) {
-            const float *src = amps + 2 * abase + (size_t)lane * (PART / 4);
-            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                         ::"r"(su32(stage + lane * PART)), "l"(src), "r"(PART), "r"(su32(bar)) : "memory");
+        // one tiled copy with the 128-byte swizzle: box {32 floats, 8 lines,
+        // 64 blocks} of the view [block][8 lines][32 floats]; x = 0, y = 0,
+        // z = first block of the tile
+        if (lane == 0) {
+            const int z = (int)(abase / K);
+            asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+                         "[%0], [%1, {%2, %3, %4}], [%5];"
+                         ::"r"(su32(stage)), "l"(tmap), "r"(0), "r"(0), "r"(z), "r"(su32(bar)) : "memory");
         }
     } else if (lane == 0) {
         // one tiled copy: box {128 floats, K mids, 1 outer} of the view
@@ -194,6 +197,13 @@ k_wht_tc(float *amps, const __grid_constant__ CUtensorMap tmap, int lo, uint64_t
     __shared__ int s_abort;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // the 128-byte swizzle of the staged tile repeats every 1024 bytes: the
+    // stage must start on such a boundary (the reads undo the pattern from
+    // offsets relative to it)
+    if (su32(stage) & 1023u) {
+        if (tid == 0) atomicExch(status, 4);
+        return;
+    }
     for (int i = tid; i < K * K / 8; i += kTcThreads) {  // W[n][k] = (-1)^popcount(n & k)
         const int n = i / (K / 8), k0 = (i % (K / 8)) * 8;
         float v[8];
@@ -243,16 +253,34 @@ k_wht_tc(float *amps, const __grid_constant__ CUtensorMap tmap, int lo, uint64_t
             for (int j = 0; j < 32; ++j) a[j] = __float_as_uint(__uint_as_float(a[j]) + __uint_as_float(b[j]));
             const int row = 32 * lg + lane;
             if (LOW) {
-                // row = output mid, registers = 16 blocks x (re, im)
+                // row = output mid, registers = 16 blocks x (re, im); lanes 2l and
+                // 2l + 1 hold mids r and r + 1: the even lane stores both for the
+                // even blocks, the odd lane for the odd blocks (16-byte stores)
+                const bool odd = lane & 1;
+                const int r0 = row & ~1;
 #pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const uint64_t a0 = abase + (uint64_t)(16 * cg + q) * K + row;
-                    float re = __uint_as_float(a[2 * q]) * scale, im = __uint_as_float(a[2 * q + 1]) * scale;
-                    if (negate_but_zero && a0 != 0) {
-                        re = -re;
-                        im = -im;
+                for (int p = 0; p < 8; ++p) {
+                    const float e0 = __uint_as_float(a[4 * p]), e1 = __uint_as_float(a[4 * p + 1]);
+                    const float o0 = __uint_as_float(a[4 * p + 2]), o1 = __uint_as_float(a[4 * p + 3]);
+                    // even lane gives its odd-block pair, odd lane its even-block pair
+                    const float g0 = __shfl_xor_sync(0xffffffffu, odd ? e0 : o0, 1);
+                    const float g1 = __shfl_xor_sync(0xffffffffu, odd ? e1 : o1, 1);
+                    // (mid r0: re, im), (mid r0 + 1: re, im) of block 2p + odd
+                    float4 v = odd ? make_float4(g0, g1, o0, o1) : make_float4(e0, e1, g0, g1);
+                    const uint64_t a0 = abase + (uint64_t)(16 * cg + 2 * p + (odd ? 1 : 0)) * K + r0;
+                    v.x *= scale;
+                    v.y *= scale;
+                    v.z *= scale;
+                    v.w *= scale;
+                    if (negate_but_zero) {
+                        if (a0 != 0) {
+                            v.x = -v.x;
+                            v.y = -v.y;
+                        }
+                        v.z = -v.z;
+                        v.w = -v.w;
                     }
-                    __stcs(reinterpret_cast<float2 *>(amps) + a0, make_float2(re, im));
+                    __stcs(reinterpret_cast<float4 *>(amps) + a0 / 2, v);
                 }
             } else {
                 // row = column (re or im of amplitude row / 2), registers = output
@@ -298,13 +326,17 @@ k_wht_tc(float *amps, const __grid_constant__ CUtensorMap tmap, int lo, uint64_t
         load_pending = false;
         if (LOW) {
             // unit = (block o, k-group of 8 mids): 8 complex = 4 float4 contiguous
+            // the stage holds 128-byte lines whose 16-byte chunks the copy
+            // permuted: chunk c of line L sits at chunk c ^ (L & 7); the eight
+            // threads of a load phase then read eight different bank groups
             for (int u = tid; u < (kCols / 2) * (K / 8); u += kTcThreads) {
                 const int kg = u % (K / 8), o = u / (K / 8);
-                const float4 *src = reinterpret_cast<const float4 *>(stage) + (size_t)o * (K / 2) + kg * 4;
                 float re[8], im[8];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const float4 c = src[q];
+                    const uint32_t logical = (uint32_t)o * (K * 8) + (uint32_t)kg * 64 + (uint32_t)q * 16;
+                    const uint32_t phys = logical ^ (((logical >> 7) & 7u) << 4);
+                    const float4 c = *reinterpret_cast<const float4 *>(stage + phys);
                     re[2 * q] = c.x;
                     im[2 * q] = c.y;
                     re[2 * q + 1] = c.z;
@@ -423,6 +455,21 @@ cudaError_t encode_upper_map(CUtensorMap *m, void *amps, int n, int lo, int kb) 
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// View of the state for the lowest group: [block of 128 amplitudes][8 lines][32
+// floats], box {32, 8, 64} with the 128-byte swizzle.
+cudaError_t encode_low_map(CUtensorMap *m, void *amps, int n) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint64_t dims[3] = {32, 8, 1ull << (n - 7)};
+    const cuuint64_t strides[2] = {128, 1024};
+    const cuuint32_t box[3] = {32u, 8u, (cuuint32_t)(kCols / 2)};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, amps, dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <int KB, bool LOW>
 cudaError_t launch_tc_t(void *amps, int n, int lo, float scale, bool negate, int *status, long long wait_limit,
                         int stall, cudaStream_t st, const Geometry &g) {
@@ -438,8 +485,8 @@ cudaError_t launch_tc_t(void *amps, int n, int lo, float scale, bool negate, int
     }
     CUtensorMap tmap;
     memset(&tmap, 0, sizeof tmap);
-    if (!LOW) {
-        cudaError_t e = encode_upper_map(&tmap, amps, n, lo, KB);
+    {
+        cudaError_t e = LOW ? encode_low_map(&tmap, amps, n) : encode_upper_map(&tmap, amps, n, lo, KB);
         if (e != cudaSuccess) return e;
     }
     const uint64_t N = 1ull << n;
