@@ -282,24 +282,30 @@ def run_ours(args):
     e2e_t, e2e_units = aggregate(e2e_elapsed, float(N) * k * e2e_steps, backend_device=dev)
 
     # the conventional circuit on the same state, for the speedup of the
-    # equivalent operator over it (a few iterations; not part of `value`)
+    # equivalent operator over it (a few iterations; not part of `value`):
+    # every engine that runs this state
     gate = None
     if args.gate_iters > 0:
-        st.init_uniform()
-        st.iterate_gate(mk, 1)  # warm-up
-        torch.cuda.synchronize()
-        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        g0.record(stream)
-        st.iterate_gate(mk, args.gate_iters)
-        g1.record(stream)
-        torch.cuda.synchronize()
-        gate_s = g0.elapsed_time(g1) / 1e3 / args.gate_iters
-        passes = 2 * ((n + 7) // 8)
-        gate = {"iterations_timed": args.gate_iters, "iteration_ms": gate_s * 1e3,
-                "value": N / gate_s, "unit": UNIT, "passes_per_iteration": passes,
-                "hbm_gbs": passes * 2 * BYTES_PER_AMP[dtype] * N / gate_s / 1e9,
-                "engine": "Walsh-Hadamard butterflies, CUDA cores",
-                "operator_speedup": gate_s / pass_s}
+        gate = {"iterations_timed": args.gate_iters, "unit": UNIT}
+        engines = [("tensor_cores", 1), ("cuda_cores", 0)] if (dtype == "c64" and n >= 13) else [("cuda_cores", 0)]
+        for name, eng in engines:
+            st.set_gate_engine(eng)
+            st.init_uniform()
+            st.iterate_gate(mk, 1)  # warm-up
+            torch.cuda.synchronize()
+            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            g0.record(stream)
+            st.iterate_gate(mk, args.gate_iters)
+            g1.record(stream)
+            torch.cuda.synchronize()
+            st.sync()
+            gate_s = g0.elapsed_time(g1) / 1e3 / args.gate_iters
+            gb = 7 if eng == 1 else 8
+            passes = 2 * ((n + gb - 1) // gb)
+            gate[name] = {"iteration_ms": gate_s * 1e3, "value": N / gate_s, "passes_per_iteration": passes,
+                          "group_bits": gb, "hbm_gbs": passes * 2 * BYTES_PER_AMP[dtype] * N / gate_s / 1e9,
+                          "operator_speedup": gate_s / pass_s}
+        st.set_gate_engine(-1)
 
     if rank != 0:
         return None
@@ -616,6 +622,87 @@ def run_phase_study(args):
             "p_bound_zalka": math.sin((2 * K + 1) * theta) ** 2, "timing": sizes}
 
 
+def _timed_events(fn, reps, stream):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3 / reps
+
+
+def run_phase_kernels(args):
+    """The phase iterator's passes where they are HBM-bound: n=26 complex64
+    (512 MiB state, 512 MiB adjoint), M=3, K=4, uniform start; forward and
+    backward sweeps timed with CUDA events; bytes per pass: forward 16 B per
+    amplitude (read + write), backward 32 B (state and adjoint)."""
+    import numpy as np
+    import torch
+    from paper_2005_04635_gb300 import binding, inputs
+    torch.cuda.set_device(0)
+    binding.lib()
+    n, m, K, seed = 26, 3, 4, 750
+    N = 1 << n
+    mk = binding.Marked(n, inputs.marked_indices(n, m, seed))
+    phi, vphi = [torch.as_tensor(x, device="cuda") for x in inputs.uniform_phases(K, seed + 1)]
+    stream = torch.cuda.current_stream()
+    st = binding.State(n, "c64", stream=stream)
+    lam = torch.empty(N, dtype=torch.complex64, device="cuda")
+    gp = torch.empty(K, dtype=torch.float64, device="cuda")
+    gv = torch.empty(K, dtype=torch.float64, device="cuda")
+    st.init_uniform()
+    for _ in range(args.warmup):
+        st.phase_forward(mk, phi, vphi, None)
+        st.phase_backward(mk, phi, vphi, lam, gp, gv)
+    fwd = _timed_events(lambda: st.phase_forward(mk, phi, vphi, None), args.steps, stream)
+    both = _timed_events(lambda: (st.phase_forward(mk, phi, vphi, None),
+                                  st.phase_backward(mk, phi, vphi, lam, gp, gv)), args.steps, stream)
+    st.sync()
+    bwd = both - fwd
+    peaks, src = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    # forward: one read-only reduction (8 B / amp) + K update passes (16 B);
+    # backward: one start pass (read psi, write lambda: 16 B) + K passes (32 B)
+    fwd_bytes = N * (8 + 16 * K)
+    bwd_bytes = N * (16 + 32 * K)
+    return {"study": "phase-kernels", "workload": f"n={n} complex64, M={m} (seed {seed}), K={K}, uniform start",
+            "forward_ms": fwd * 1e3, "backward_ms": bwd * 1e3,
+            "forward_gbs": fwd_bytes / fwd / 1e9, "backward_gbs": bwd_bytes / bwd / 1e9,
+            "forward_frac": fwd_bytes / fwd / 1e9 / hbm, "backward_frac": bwd_bytes / bwd / 1e9 / hbm,
+            "peak": f"{hbm} GB/s ({src})"}
+
+
+def run_gate_kernels(args):
+    """The conventional circuit on the tensor cores where it is HBM-bound:
+    n=26 complex64 (512 MiB), M=1, uniform start; per-iteration time of
+    grover_iterate_gate (oracle + 8 Walsh-Hadamard passes of 7-, 7-, 7- and
+    5-bit groups, twice) with CUDA events."""
+    import torch
+    from paper_2005_04635_gb300 import binding, inputs
+    torch.cuda.set_device(0)
+    binding.lib()
+    n, m, seed = 26, 1, 2601
+    N = 1 << n
+    mk = binding.Marked(n, inputs.marked_indices(n, m, seed))
+    stream = torch.cuda.current_stream()
+    out = {"study": "gate-kernels", "workload": f"n={n} complex64, M={m} (seed {seed}), uniform start"}
+    for name, eng, gb in (("tensor_cores", 1, 7), ("cuda_cores", 0, 8)):
+        st = binding.State(n, "c64", stream=stream)
+        st.set_gate_engine(eng)
+        st.init_uniform()
+        for _ in range(args.warmup):
+            st.iterate_gate(mk, 1)
+        t = _timed_events(lambda: st.iterate_gate(mk, 1), args.steps, stream)
+        st.sync()
+        passes = 2 * ((n + gb - 1) // gb)
+        out[name] = {"iteration_ms": t * 1e3, "passes": passes, "pass_gbs": passes * 16 * N / t / 1e9}
+        del st
+    return out
+
+
 # ---- reference arm: the oracle on the host cores -----------------------------------------------------
 def run_reference(args):
     rank, world, local = dist_env()
@@ -683,7 +770,7 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched-4096"], default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--study", choices=["precision", "phase"], default=None,
+    ap.add_argument("--study", choices=["precision", "phase", "phase-kernels", "gate-kernels"], default=None,
                     help="run a study instead of the throughput benchmark")
     ap.add_argument("--gate-iters", type=int, default=2,
                     help="iterations of the conventional circuit timed for comparison (0: skip)")
@@ -696,6 +783,10 @@ def main(argv=None):
         out = run_precision_study(args)
     elif args.study == "phase":
         out = run_phase_study(args)
+    elif args.study == "phase-kernels":
+        out = run_phase_kernels(args)
+    elif args.study == "gate-kernels":
+        out = run_gate_kernels(args)
     elif args.workload == "batched-4096" and args.impl != "reference":
         out = run_batched(args)
     else:
