@@ -13,6 +13,8 @@ of Grover's quantum search on classical computer" (arXiv 2005.04635):
 * ``grover_gate``      -- conventional grover_search (section "Background"):
   oracle, H^{(x)n} (Eq. unitary, Algorithm "1-qubit Unitary Operation"),
   2|0><0| - I, H^{(x)n}.
+* ``grover_circuit``   -- the same circuit gate by gate, the oracle built as in
+  Fig. oracle1 (X-conjugated multi-controlled gate, phase kickback).
 * ``closed_form_uniform`` / ``closed_form_general`` -- the rotation picture of
   G = (2|psi><psi| - I) O used as a pin and as the large-n reference.
 """
@@ -53,6 +55,9 @@ def _load():
         "or_hadamard_all": (None, [_dp, ctypes.c_int]),
         "or_phase_shift_zero": (None, [_dp, ctypes.c_int]),
         "or_grover_gate": (None, [_dp, ctypes.c_int, _u64p, ctypes.c_size_t, ctypes.c_uint64]),
+        "or_x_qubit": (None, [_dp, ctypes.c_int, ctypes.c_int]),
+        "or_mcz": (None, [_dp, ctypes.c_int, ctypes.c_int]),
+        "or_grover_circuit": (ctypes.c_uint64, [_dp, ctypes.c_int, _u64p, ctypes.c_size_t, ctypes.c_uint64]),
         "or_optimal_iterations": (ctypes.c_uint64, [ctypes.c_int, ctypes.c_uint64]),
         "or_closed_form_uniform": (None, [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, _dp, _dp]),
         "or_closed_form_general": (None, [_dp, ctypes.c_int, _u64p, ctypes.c_size_t, ctypes.c_uint64]),
@@ -163,6 +168,23 @@ def grover_gate(psi, n, marked, k):
     m = _marked(marked)
     _load().or_grover_gate(_dptr(_state(psi, n)), n, _u64ptr(m), m.size, int(k))
     return psi
+
+
+def x_qubit(psi, n, q):
+    _load().or_x_qubit(_dptr(_state(psi, n)), n, q)
+    return psi
+
+
+def mcz(psi, n, negate_all=False):
+    _load().or_mcz(_dptr(_state(psi, n)), n, 1 if negate_all else 0)
+    return psi
+
+
+def grover_circuit(psi, n, marked, k):
+    """Conventional circuit gate by gate (Fig. oracle1 oracle); returns (psi, gates)."""
+    m = _marked(marked)
+    g = _load().or_grover_circuit(_dptr(_state(psi, n)), n, _u64ptr(m), m.size, int(k))
+    return psi, int(g)
 
 
 # ---- iteration count, closed forms --------------------------------------------

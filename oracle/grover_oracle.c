@@ -181,6 +181,60 @@ void or_phase_shift_zero(double *psi, int n) {
 }
 
 /* Conventional grover_search: oracle, H^{(x)n}, 2|0><0|-I, H^{(x)n}. */
+/* Pauli X on qubit q: the amplitudes of x and x ^ 2^q trade places. */
+void or_x_qubit(double *psi, int n, int q) {
+    uint64_t N = dim(n);
+    uint64_t s = (uint64_t)1 << q;
+    for (uint64_t x = 0; x < N; ++x) {
+        if (x & s) continue;
+        uint64_t y = x | s;
+        for (int c = 0; c < 2; ++c) {
+            double t = psi[2 * x + c];
+            psi[2 * x + c] = psi[2 * y + c];
+            psi[2 * y + c] = t;
+        }
+    }
+}
+
+/* Multi-controlled Z on all n qubits: phase -1 on |1...1>, visiting every
+ * amplitude as a gate-level simulator does (one O(N) pass); negate_all also
+ * multiplies the whole state by -1. */
+void or_mcz(double *psi, int n, int negate_all) {
+    uint64_t N = dim(n);
+    for (uint64_t x = 0; x < N; ++x) {
+        int flip = (x == N - 1);
+        if (negate_all) flip = !flip;
+        if (flip) {
+            psi[2 * x] = -psi[2 * x];
+            psi[2 * x + 1] = -psi[2 * x + 1];
+        }
+    }
+}
+
+uint64_t or_grover_circuit(double *psi, int n, const uint64_t *marked, size_t m, uint64_t k) {
+    uint64_t gates = 0;
+    for (uint64_t it = 0; it < k; ++it) {
+        /* oracle, Fig. oracle1: X on each qubit where the solution has a 0,
+         * the multi-controlled gate, the same X gates again */
+        for (size_t i = 0; i < m; ++i) {
+            for (int q = 0; q < n; ++q)
+                if (!((marked[i] >> q) & 1)) { or_x_qubit(psi, n, q); ++gates; }
+            or_mcz(psi, n, 0);
+            ++gates;
+            for (int q = 0; q < n; ++q)
+                if (!((marked[i] >> q) & 1)) { or_x_qubit(psi, n, q); ++gates; }
+        }
+        for (int q = 0; q < n; ++q) { or_hadamard_qubit(psi, n, q); ++gates; }
+        /* 2|0><0| - I = -X^{(x)n} (I - 2|1...1><1...1|) X^{(x)n} */
+        for (int q = 0; q < n; ++q) { or_x_qubit(psi, n, q); ++gates; }
+        or_mcz(psi, n, 1);
+        ++gates;
+        for (int q = 0; q < n; ++q) { or_x_qubit(psi, n, q); ++gates; }
+        for (int q = 0; q < n; ++q) { or_hadamard_qubit(psi, n, q); ++gates; }
+    }
+    return gates;
+}
+
 void or_grover_gate(double *psi, int n, const uint64_t *marked, size_t m,
                     uint64_t k) {
     for (uint64_t it = 0; it < k; ++it) {

@@ -65,6 +65,22 @@ void or_phase_shift_zero(double *psi, int n);
 void or_grover_gate(double *psi, int n, const uint64_t *marked, size_t m,
                     uint64_t k);
 
+/* ---- the conventional circuit gate by gate (section "Background",
+ *      Fig. oracle1; cost model O([f_o(n) + f_c(n) + 2n] N^{3/2})) ------- */
+/* Pauli X on qubit q. */
+void or_x_qubit(double *psi, int n, int q);
+/* Multi-controlled Z on all n qubits (phase -1 on |1...1>): the action on the
+ * register of Fig. oracle1's multi-controlled NOT onto an ancilla prepared in
+ * (|0> - |1>)/sqrt(2) (phase kickback).  negate_all: also multiply the whole
+ * state by -1.  One pass over all N amplitudes. */
+void or_mcz(double *psi, int n, int negate_all);
+/* k iterations, one gate (one pass) at a time: the oracle for each marked s
+ * as X on every qubit where s has a 0, MCZ, the same X gates (f_o = sum over
+ * marked s of 2 zeros(s) + 1); H^{(x)n} as n single-qubit Hadamards; the
+ * phase shift 2|0><0| - I as X^{(x)n}, -MCZ, X^{(x)n} (f_c = 2n + 1); H^{(x)n}.
+ * Returns the number of gates applied. */
+uint64_t or_grover_circuit(double *psi, int n, const uint64_t *marked, size_t m, uint64_t k);
+
 /* ---- iteration count, closed forms ------------------------------------- */
 /* floor(pi/4 * sqrt(N/M)); 0 when m == 0. */
 uint64_t or_optimal_iterations(int n, uint64_t m);

@@ -392,3 +392,90 @@ def test_phase_reduced_model_at_pi_is_the_closed_form(n, m, K):
     b = (-1) ** K * math.cos((2 * K + 1) * theta) / math.sqrt((1 << n) - m)
     assert abs(alpha - a) <= 1e-12 * max(1.0, abs(a)) * K and abs(beta - b) <= 1e-12 * K / math.sqrt(1 << n) + 1e-15
     assert abs(loss + math.log(m * a * a)) <= 1e-10
+
+
+# --- the conventional circuit gate by gate (Fig. oracle1) ---------------------------------
+def _dense_x(n, q):
+    N = 1 << n
+    X = np.zeros((N, N))
+    for x in range(N):
+        X[x ^ (1 << q), x] = 1.0
+    return X
+
+
+def test_x_and_mcz_against_dense():
+    n = 4
+    N = 1 << n
+    psi0 = inputs.gaussian_state(n, seed=21)
+    for q in range(n):
+        got = oracle.x_qubit(psi0.copy(), n, q)
+        assert np.array_equal(got, _dense_x(n, q) @ psi0)
+    Z = np.eye(N)
+    Z[N - 1, N - 1] = -1.0
+    assert np.array_equal(oracle.mcz(psi0.copy(), n), Z @ psi0)
+    assert np.array_equal(oracle.mcz(psi0.copy(), n, negate_all=True), -(Z @ psi0))
+
+
+@pytest.mark.parametrize("s", [0, 1, 2, 3])
+def test_fig_oracle1_two_qubit_cases(s):
+    """Fig. oracle1: for solution |s> of 2 qubits, X on the qubits where s has
+    a 0, the multi-controlled gate, the same X: O = I - 2|s><s| on every basis
+    state, with 2 zeros(s) X gates (|00>: 4, |01> and |10>: 2, |11>: 0)."""
+    n = 2
+    for x in range(4):
+        e = np.zeros(4, dtype=np.complex128)
+        e[x] = 1.0
+        got, gates = oracle.grover_circuit(e.copy(), n, [s], 0)
+        assert gates == 0
+        # apply just the oracle part: X pattern, MCZ, X pattern
+        for q in range(n):
+            if not (s >> q) & 1:
+                oracle.x_qubit(e, n, q)
+        oracle.mcz(e, n)
+        for q in range(n):
+            if not (s >> q) & 1:
+                oracle.x_qubit(e, n, q)
+        want = np.zeros(4)
+        want[x] = -1.0 if x == s else 1.0
+        assert np.array_equal(e.real, want) and not np.any(e.imag)
+
+
+@pytest.mark.parametrize("n,m,k", [(3, 1, 2), (5, 2, 3), (9, 3, 4), (12, 4, 5)])
+def test_circuit_equals_operator_and_gate_form(n, m, k):
+    marked = inputs.marked_indices(n, m, seed=30 + n)
+    psi0 = inputs.gaussian_state(n, seed=31 + n)
+    got, gates = oracle.grover_circuit(psi0.copy(), n, marked, k)
+    ref = oracle.grover_operator(psi0.copy(), n, marked, k)
+    assert np.max(np.abs(got - ref)) <= 1e-13
+    zeros = sum(n - bin(int(x)).count("1") for x in marked)
+    assert gates == k * ((2 * zeros + m) + 2 * n + (2 * n + 1))
+
+
+def test_circuit_dense_product_n4():
+    """One iteration equals the dense product of its gate list."""
+    n, marked = 4, [5, 12]
+    N = 1 << n
+    Hs = [np.kron(np.kron(np.eye(1 << (n - 1 - q)), np.array([[1, 1], [1, -1]]) / math.sqrt(2)), np.eye(1 << q))
+          for q in range(n)]
+    Z = np.eye(N)
+    Z[N - 1, N - 1] = -1.0
+    U = np.eye(N)
+    for s in marked:
+        Xs = [_dense_x(n, q) for q in range(n) if not (s >> q) & 1]
+        for X in Xs:
+            U = X @ U
+        U = Z @ U
+        for X in Xs:
+            U = X @ U
+    for H in Hs:
+        U = H @ U
+    for q in range(n):
+        U = _dense_x(n, q) @ U
+    U = -Z @ U
+    for q in range(n):
+        U = _dense_x(n, q) @ U
+    for H in Hs:
+        U = H @ U
+    psi0 = inputs.gaussian_state(n, seed=40)
+    got, _ = oracle.grover_circuit(psi0.copy(), n, marked, 1)
+    assert np.max(np.abs(got - U @ psi0)) <= 1e-14
