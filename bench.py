@@ -306,6 +306,22 @@ def run_ours(args):
                           "group_bits": gb, "hbm_gbs": passes * 2 * BYTES_PER_AMP[dtype] * N / gate_s / 1e9,
                           "operator_speedup": gate_s / pass_s}
         st.set_gate_engine(-1)
+        # gate by gate (one pass per single-qubit gate, Fig. oracle1 oracle):
+        # the paper's (f_o + f_c + 2n)-gate cost model; one iteration
+        st.init_uniform()
+        st.iterate_circuit(mk, 1)  # warm-up
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        gates, passes = st.iterate_circuit(mk, 1)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        st.sync()
+        gate_s = g0.elapsed_time(g1) / 1e3
+        gate["gate_by_gate"] = {"iteration_ms": gate_s * 1e3, "value": N / gate_s, "gates_per_iteration": gates,
+                                "passes_per_iteration": passes,
+                                "hbm_gbs": passes * 2 * BYTES_PER_AMP[dtype] * N / gate_s / 1e9,
+                                "operator_speedup": gate_s / pass_s}
 
     if rank != 0:
         return None

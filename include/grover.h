@@ -213,6 +213,26 @@ grover_status grover_iterate(grover_state *s, const grover_marked *mk, uint64_t 
  * that gives up is reported by grover_sync (GROVER_ETIMEOUT). */
 grover_status grover_iterate_gate(grover_state *s, const grover_marked *mk, uint64_t k);
 
+/* k iterations of the conventional circuit GATE BY GATE, the way a gate-level
+ * state-vector simulator runs it (section "Background", cost model
+ * O([f_o(n) + f_c(n) + 2n] N^{3/2})): every single-qubit gate is one pass over
+ * the state (Algorithm "1-qubit Unitary Operation").
+ *   oracle      for each marked s (Fig. oracle1): X on every qubit where s has
+ *               a 0, a multi-controlled Z on all n qubits (the register side
+ *               of the multi-controlled NOT onto an ancilla in
+ *               (|0> - |1>)/sqrt(2); it touches the single amplitude |1...1>),
+ *               the same X gates again: f_o = sum_s (2 zeros(s) + 1) gates;
+ *   H^{(x)n}    n Hadamards, scale 1/sqrt(2) rounded to the state's type;
+ *   2|0><0| - I X^{(x)n}, MCZ, X^{(x)n} and a global -1 (carried by the next
+ *               Hadamard's scale): f_c = 2n + 1 gates;
+ *   H^{(x)n}.
+ * gates_out / passes_out (optional, host): gates applied (the paper's count
+ * f_o + f_c + 2n per iteration) and full passes over the state among them.
+ * The marked set must be built from a list (GROVER_EUNSUPPORTED for bitmask
+ * sets, whose indices are not on the host).  Asynchronous on the stream. */
+grover_status grover_iterate_circuit(grover_state *s, const grover_marked *mk, uint64_t k,
+                                     uint64_t *gates_out, uint64_t *passes_out);
+
 /* floor(pi/4 * sqrt(2^n / m)), the iteration count that maximises the success
  * probability for m marked states out of 2^n (the paper's loop bound
  * pi*sqrt(N)/4 read as a floor, generalised to m solutions); 0 if m == 0 or

@@ -40,6 +40,8 @@ _SIGS = {
     "grover_diffuse": (ctypes.c_int, [_vp]),
     "grover_iterate": (ctypes.c_int, [_vp, _vp, ctypes.c_uint64]),
     "grover_iterate_gate": (ctypes.c_int, [_vp, _vp, ctypes.c_uint64]),
+    "grover_iterate_circuit": (ctypes.c_int, [_vp, _vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64),
+                                              ctypes.POINTER(ctypes.c_uint64)]),
     "grover_optimal_iterations": (ctypes.c_uint64, [ctypes.c_int, ctypes.c_uint64]),
     "grover_measure_probs": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
     "grover_measure_topm": (ctypes.c_int, [_vp, ctypes.c_size_t, _vp, _vp]),
@@ -203,6 +205,13 @@ class State:
 
     def iterate_gate(self, marked: Marked, k: int):
         _check(lib().grover_iterate_gate(self.handle, marked.handle, int(k)), self.handle)
+
+    def iterate_circuit(self, marked: Marked, k: int):
+        """Conventional circuit gate by gate; returns (gates, full passes)."""
+        g, p = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(lib().grover_iterate_circuit(self.handle, marked.handle, int(k), ctypes.byref(g), ctypes.byref(p)),
+               self.handle)
+        return int(g.value), int(p.value)
 
     def measure_probs(self, out=None):
         """Returns p_i = |c_i|^2 (FP64): into a CUDA tensor if given, else a numpy array."""

@@ -304,6 +304,12 @@ grover_status grover_marked_from_list(grover_marked **out, int n, const uint64_t
         }
         mk->dev.list = (const uint64_t *)mk->list_mem;
         mk->dev.mode = MARK_LIST;
+        mk->host_list = (uint64_t *)malloc(m * sizeof(uint64_t));
+        if (!mk->host_list) {
+            grover_marked_destroy(mk);
+            return fail(nullptr, GROVER_ENOMEM, "host copy of the marked list");
+        }
+        memcpy(mk->host_list, idx, m * sizeof(uint64_t));
     }
     if (m > kListMax) {
         const uint64_t nwords = (N + 31) / 32;
@@ -374,6 +380,7 @@ grover_status grover_marked_destroy(grover_marked *mk) {
     cudaError_t e = cudaDeviceSynchronize();
     if (mk->list_mem) cudaFree(mk->list_mem);
     if (mk->words_mem) cudaFree(mk->words_mem);
+    free(mk->host_list);
     free(mk);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "grover_marked_destroy");
     return GROVER_OK;
@@ -518,6 +525,63 @@ grover_status grover_iterate_gate(grover_state *s, const grover_marked *mk, uint
             }
         }
     }
+    return GROVER_OK;
+}
+
+grover_status grover_iterate_circuit(grover_state *s, const grover_marked *mk, uint64_t k, uint64_t *gates_out,
+                                     uint64_t *passes_out) {
+    if (grover_status st = check_state(s)) return st;
+    if (grover_status st = check_marked(s, mk)) return st;
+    if (mk->dev.m > 0 && !mk->host_list)
+        return fail(s, GROVER_EUNSUPPORTED, "the gate-by-gate oracle needs a marked set built from a list");
+    const double r = 0.70710678118654752440;  // 1/sqrt(2)
+    uint64_t gates = 0, passes = 0;
+    s->mu_valid = false;
+    for (uint64_t t = 0; t < k; ++t) {
+        // oracle (Fig. oracle1): X where the solution has a 0, MCZ, the same X
+        for (uint64_t i = 0; i < mk->dev.m; ++i) {
+            const uint64_t x = mk->host_list[i];
+            for (int pass = 0; pass < 2; ++pass) {
+                for (int q = 0; q < s->n; ++q) {
+                    if ((x >> q) & 1) continue;
+                    CK(s, launch_gate1(s->amps, s->n, s->dtype, 0, q, 1.0, s->stream, s->geo), "X gate launch");
+                    ++gates;
+                    ++passes;
+                }
+                if (pass == 0) {
+                    CK(s, launch_mcz_all(s->amps, s->n, s->dtype, s->stream), "MCZ launch");
+                    ++gates;
+                }
+            }
+        }
+        // H^{(x)n}
+        for (int q = 0; q < s->n; ++q) {
+            CK(s, launch_gate1(s->amps, s->n, s->dtype, 1, q, r, s->stream, s->geo), "H gate launch");
+            ++gates;
+            ++passes;
+        }
+        // 2|0><0| - I = -X^{(x)n} MCZ X^{(x)n}; the -1 rides on the next H
+        for (int q = 0; q < s->n; ++q) {
+            CK(s, launch_gate1(s->amps, s->n, s->dtype, 0, q, 1.0, s->stream, s->geo), "X gate launch");
+            ++gates;
+            ++passes;
+        }
+        CK(s, launch_mcz_all(s->amps, s->n, s->dtype, s->stream), "MCZ launch");
+        ++gates;
+        for (int q = 0; q < s->n; ++q) {
+            CK(s, launch_gate1(s->amps, s->n, s->dtype, 0, q, 1.0, s->stream, s->geo), "X gate launch");
+            ++gates;
+            ++passes;
+        }
+        // H^{(x)n}, the first Hadamard also carrying the phase shift's -1
+        for (int q = 0; q < s->n; ++q) {
+            CK(s, launch_gate1(s->amps, s->n, s->dtype, 1, q, q == 0 ? -r : r, s->stream, s->geo), "H gate launch");
+            ++gates;
+            ++passes;
+        }
+    }
+    if (gates_out) *gates_out = gates;
+    if (passes_out) *passes_out = passes;
     return GROVER_OK;
 }
 

@@ -164,6 +164,14 @@ cudaError_t launch_wht_tc_pass(void *amps, int n, int lo, int kb, bool scaled, b
                                long long wait_limit, int stall, cudaStream_t st, const Geometry &g);
 constexpr long long kDefaultWaitLimit = 1ll << 22;  // mbarrier polls (~0.4 s)
 
+// ---- conventional circuit gate by gate (k_circuit.cu) ------------------------
+// One single-qubit gate as one pass: op 0 = X, op 1 = H scaled by `scale`
+// (+-1/sqrt(2)).
+cudaError_t launch_gate1(void *amps, int n, grover_dtype dt, int op, int q, double scale, cudaStream_t st,
+                         const Geometry &g);
+// Multi-controlled Z on all n qubits: negates the amplitude |1...1>.
+cudaError_t launch_mcz_all(void *amps, int n, grover_dtype dt, cudaStream_t st);
+
 // ---- batched searches (k_batch.cu) ------------------------------------------
 constexpr uint32_t kBatchMaxMarked = 64;  // marked indices per instance
 constexpr int kBatchMaxQubits = 26;
@@ -262,4 +270,5 @@ struct grover_marked {
     grv::MarkedDev dev;
     void *list_mem;
     void *words_mem;
+    uint64_t *host_list;    // host copy of a list-built set (the gate-by-gate oracle reads its bits)
 };
