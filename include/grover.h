@@ -138,8 +138,9 @@ typedef enum {
     GROVER_OPT_WAIT_LIMIT = 2,
     /* Test hook for those failure paths: 1 makes the next tensor-core pass
      * of grover_iterate_gate withhold its MMA completion signal, or the next
-     * grid persistent iterator launch withhold CTA 0's first partial, so a
-     * wait runs out (reset to 0 once used).  Not for production use. */
+     * grid persistent launch (grover_iterate, or an on-chip phase sweep)
+     * withhold CTA 0's first partial, so a wait runs out (reset to 0 once
+     * used).  Not for production use. */
     GROVER_OPT_TEST_STALL = 3
 } grover_option;
 
@@ -346,8 +347,12 @@ grover_status grover_iterate_noalloc(void *dev_amps, int n_qubits, grover_dtype 
  * iterations.  Complex64 states only; the marked set must be a list of 1 to
  * 256 indices (grover_marked_from_list), else GROVER_EUNSUPPORTED.  Means are
  * exact sums of the FP32 amplitudes rounded once to FP64; phase factors are
- * computed in FP64 and applied in FP32.  One pass over the state per iteration
- * plus one initial reduction.
+ * computed in FP64 and applied in FP32.  Where the state fits the SMs' shared
+ * memory (GB300: n <= 22) and GROVER_OPT_RESIDENT is not 0, the whole sweep is
+ * one cooperative launch with the state on chip (per-iteration sums exchanged
+ * exactly through global memory, bounded waits: GROVER_ETIMEOUT at
+ * grover_sync if one runs out); otherwise one pass over the state per
+ * iteration plus one initial reduction.
  *
  *   phi, vphi  DEVICE arrays of K doubles (radians) on the state's device,
  *              read by the kernels when they run (stream order).
@@ -372,7 +377,10 @@ grover_status grover_phase_forward(grover_state *s, const grover_marked *mk, con
  *   grad_phi, grad_vphi  DEVICE arrays of K doubles, overwritten.
  *
  * On completion the handle's state holds psi_0 up to FP32 rounding (about K
- * units of roundoff).  K + 1 passes; enqueued on the handle's stream. */
+ * units of roundoff).  On chip in one launch where the state and the adjoint
+ * fit (GB300: n <= 21; the adjoint is carried as sqrt(P) lambda there, so its
+ * sums stay in the fixed-point window), else K + 1 passes; enqueued on the
+ * handle's stream. */
 grover_status grover_phase_backward(grover_state *s, const grover_marked *mk, const double *phi,
                                     const double *vphi, uint64_t K, void *lam, double *grad_phi,
                                     double *grad_vphi);

@@ -235,6 +235,35 @@ cudaError_t launch_phase_bwd(const PhaseArgs &a, bool stream, cudaStream_t st, i
 // lambda_K from psi_K, dL/dvphi_{K-1} and the constants of backward pass K-1.
 cudaError_t launch_phase_bwd_start(const PhaseArgs &a, bool stream, cudaStream_t st, int sm_count);
 
+// ---- the phase iterator kept on chip (k_phase_grid.cu), complex64 ------------
+constexpr size_t kPhaseGridSmemMax = 232448 - 8192;  // dynamic shared memory per CTA (227 KiB less static)
+struct PhaseGridArgs {
+    void *psi;                  // state (forward: psi_0 -> psi_K; backward: psi_K -> psi_0)
+    void *lam;                  // adjoint output lambda_0 (backward)
+    uint64_t nvec;              // 16-byte vectors
+    uint32_t slice_vecs;        // vectors per CTA (the last may hold fewer)
+    int n;
+    const uint64_t *list;       // sorted marked indices
+    uint32_t m;
+    const double *phi, *vphi;   // [K] phases (device)
+    long long K;
+    unsigned long long *region; // exchange region (accumulators + counter zeroed before the launch)
+    double *stats;              // forward: [2] P, -log P, or NULL
+    double *grad_phi, *grad_vphi;  // backward: [K]
+    int *status;                // 3 if a wait runs out
+    long long wait_limit;
+    int stall;                  // test hook: CTA 0 withholds its first contribution
+    const double2 *table;       // [2K]: e^{i phi_t}, e^{i vphi_t} as (cos, sin), or NULL
+};
+constexpr long long kPhaseTableMax = 1ll << 14;  // table entries kept in the handle's scratch
+// Fills table[2t] = e^{i phi_t}, table[2t + 1] = e^{i vphi_t} as (cos, sin) in FP64.
+cudaError_t launch_phase_table(const double *phi, const double *vphi, long long K, double2 *table, cudaStream_t st);
+// false if the state (backward: state and adjoint) does not fit the SMs' shared memory
+bool phase_grid_plan(int n, bool backward, int sm_count, unsigned *G, uint32_t *slice_vecs, size_t *smem);
+size_t phase_grid_region_bytes(unsigned G);  // whole exchange region
+size_t phase_grid_zero_bytes();              // its part that must be zero at launch
+cudaError_t launch_phase_grid(const PhaseGridArgs &a, bool backward, unsigned G, size_t smem, cudaStream_t st);
+
 // ---- errors (grover_api.cu) ------------------------------------------------
 // Sets the message grover_last_error(NULL) returns on this host thread.
 void set_thread_error(const char *msg);

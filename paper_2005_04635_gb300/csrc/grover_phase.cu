@@ -30,25 +30,31 @@ struct PhaseScratch {
     PhaseConst *c;      // [2] constants, ping-pong between passes
     unsigned *ticket;   // [1]
     double2 *partials;  // [6 * kPhaseMaxGrid]
+    unsigned long long *region;  // exchange region of the on-chip sweeps
+    double2 *table;              // [2 kPhaseTableMax] phase factors of the on-chip sweeps
 };
 constexpr size_t kPhOffTicket = 256, kPhOffPartials = 512;
-constexpr size_t kPhBytes = kPhOffPartials + sizeof(double2) * 6 * (size_t)kPhaseMaxGrid;
+constexpr size_t kPhOffRegion = kPhOffPartials + sizeof(double2) * 6 * (size_t)kPhaseMaxGrid;
+size_t ph_off_table() { return (kPhOffRegion + phase_grid_region_bytes(512) + 255) & ~(size_t)255; }
+size_t ph_bytes() { return ph_off_table() + sizeof(double2) * 2 * (size_t)kPhaseTableMax; }
 static_assert(2 * sizeof(PhaseConst) <= kPhOffTicket, "phase constants overflow their slot");
 
 grover_status phase_scratch(grover_state *s, PhaseScratch *out) {
     if (!s->phase_mem) {
-        cudaError_t e = cudaMalloc(&s->phase_mem, kPhBytes);
+        cudaError_t e = cudaMalloc(&s->phase_mem, ph_bytes());
         if (e != cudaSuccess) {
             s->phase_mem = nullptr;
             return pfail(s, GROVER_ECUDA, "cudaMalloc(phase scratch)", e);
         }
-        if ((e = cudaMemsetAsync(s->phase_mem, 0, kPhBytes, s->stream)) != cudaSuccess)
+        if ((e = cudaMemsetAsync(s->phase_mem, 0, ph_bytes(), s->stream)) != cudaSuccess)
             return pfail(s, GROVER_ECUDA, "cudaMemsetAsync(phase scratch)", e);
     }
     char *b = (char *)s->phase_mem;
     out->c = (PhaseConst *)b;
     out->ticket = (unsigned *)(b + kPhOffTicket);
     out->partials = (double2 *)(b + kPhOffPartials);
+    out->region = (unsigned long long *)(b + kPhOffRegion);
+    out->table = (double2 *)(b + ph_off_table());
     return GROVER_OK;
 }
 
@@ -97,6 +103,47 @@ PhaseArgs base_args(grover_state *s, const grover_marked *mk, const double *phi,
     return a;
 }
 
+// The on-chip sweep (one cooperative launch) where the state -- backward: the
+// state and the adjoint -- fits the SMs' shared memory, unless the handle's
+// GROVER_OPT_RESIDENT is 0.  Returns cudaErrorNotSupported when it does not
+// apply, so the caller runs the pass kernels.
+cudaError_t try_grid(grover_state *s, const grover_marked *mk, const double *phi, const double *vphi, uint64_t K,
+                     const PhaseScratch &ps, bool backward, void *lam, double *gphi, double *gvphi, double *stats) {
+    unsigned G = 0;
+    uint32_t L = 0;
+    size_t smem = 0;
+    if (s->resident == 0 || !phase_grid_plan(s->n, backward, s->geo.sm_count, &G, &L, &smem))
+        return cudaErrorNotSupported;
+    PhaseGridArgs g;
+    memset(&g, 0, sizeof g);
+    g.psi = s->amps;
+    g.lam = lam;
+    g.nvec = s->N / 2;
+    g.slice_vecs = L;
+    g.n = s->n;
+    g.list = mk->dev.list;
+    g.m = (uint32_t)mk->dev.m;
+    g.phi = phi;
+    g.vphi = vphi;
+    g.K = (long long)K;
+    g.region = ps.region;
+    g.stats = stats;
+    g.grad_phi = gphi;
+    g.grad_vphi = gvphi;
+    g.status = s->sc.status;
+    g.wait_limit = s->wait_limit;
+    g.stall = s->test_stall;
+    cudaError_t e = cudaMemsetAsync(ps.region, 0, phase_grid_zero_bytes(), s->stream);
+    if (e != cudaSuccess) return e;
+    if (K <= (uint64_t)kPhaseTableMax) {
+        if ((e = launch_phase_table(phi, vphi, (long long)K, ps.table, s->stream)) != cudaSuccess) return e;
+        g.table = ps.table;
+    }
+    e = launch_phase_grid(g, backward, G, smem, s->stream);
+    if (e == cudaSuccess) s->test_stall = 0;
+    return e;
+}
+
 }  // namespace
 
 extern "C" {
@@ -109,6 +156,10 @@ grover_status grover_phase_forward(grover_state *s, const grover_marked *mk, con
     PhaseScratch ps;
     if (grover_status st = phase_scratch(s, &ps)) return st;
     s->mu_valid = false;
+    cudaError_t eg = try_grid(s, mk, phi, vphi, K, ps, false, nullptr, nullptr, nullptr, stats);
+    if (eg == cudaSuccess) return GROVER_OK;
+    (void)cudaGetLastError();
+    if (eg != cudaErrorNotSupported && s->resident >= 1) return pfail(s, GROVER_ECUDA, "on-chip phase sweep launch", eg);
     PhaseArgs a = base_args(s, mk, phi, vphi, K, ps);
     a.stats = stats;
     a.t = -1;
@@ -142,6 +193,10 @@ grover_status grover_phase_backward(grover_state *s, const grover_marked *mk, co
     PhaseScratch ps;
     if (grover_status st = phase_scratch(s, &ps)) return st;
     s->mu_valid = false;
+    cudaError_t eg = try_grid(s, mk, phi, vphi, K, ps, true, lam, grad_phi, grad_vphi, nullptr);
+    if (eg == cudaSuccess) return GROVER_OK;
+    (void)cudaGetLastError();
+    if (eg != cudaErrorNotSupported && s->resident >= 1) return pfail(s, GROVER_ECUDA, "on-chip adjoint sweep launch", eg);
     PhaseArgs a = base_args(s, mk, phi, vphi, K, ps);
     a.lam = lam;
     a.grad_phi = grad_phi;

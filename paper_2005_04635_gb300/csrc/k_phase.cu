@@ -23,6 +23,7 @@
 // amplitudes added as 128-bit fixed point (fixed_sum.cuh).
 #include "fixed_sum.cuh"
 #include "grover_internal.cuh"
+#include "phase_ops.cuh"
 
 namespace grv {
 namespace {
@@ -83,31 +84,13 @@ template <bool STREAM> __device__ __forceinline__ void stv(float4 *p, float4 v) 
     else *p = v;
 }
 
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-__device__ __forceinline__ double2 dcmul(double2 a, double2 b) {
-    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-__device__ __forceinline__ double2 expi(double a) {
-    double s, c;
-    sincos(a, &s, &c);
-    return make_double2(c, s);
-}
-__device__ __forceinline__ float4 split_hilo(double2 v) {
-    const float hr = (float)v.x, hi = (float)v.y;
-    return make_float4(hr, (float)(v.x - (double)hr), hi, (float)(v.y - (double)hi));
-}
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-template <int G> __device__ __forceinline__ float pairwise(const float *v) {
-    if constexpr (G == 1) return v[0];
-    else return pairwise<G / 2>(v) + pairwise<G / 2>(v + G / 2);
-}
+using ph::cmul;
+using ph::dcmul;
+using ph::expi;
+using ph::pairwise;
+using ph::split_hilo;
+using ph::sub_hilo;
+using ph::warp_sum_d;
 
 // Grid sums of NS complex fixed-point accumulators, in two steps.
 // grid_arrive: every CTA reduces its accumulators (integers exactly, FP64
@@ -261,10 +244,6 @@ __device__ void grid_total(const double2 *partials, unsigned *ticket, double2 (&
 // grid total: e^{i a} for two angles (lanes 0, 1 of warp 1).
 __device__ __forceinline__ void side_expi(double a0, double a1, double2 *out) {
     if ((threadIdx.x >> 5) == 1 && (threadIdx.x & 31) < 2) out[threadIdx.x & 1] = expi((threadIdx.x & 1) ? a1 : a0);
-}
-
-__device__ __forceinline__ float2 sub_hilo(float2 c, float4 k) {
-    return make_float2((c.x - k.x) - k.y, (c.y - k.z) - k.w);
 }
 
 // ---- forward pass ----------------------------------------------------------

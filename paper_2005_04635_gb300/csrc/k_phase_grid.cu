@@ -1,0 +1,514 @@
+// k_phase_grid.cu -- the phase iterator and its adjoint with the state kept in
+// shared memory across all SMs (complex64, states that fit on chip).
+//
+// Same arithmetic as k_phase.cu (oracle phase e^{i phi_t} on marked
+// amplitudes, c <- c - (1 - e^{i vphi_t}) <c>; adjoint through the inverse
+// iterators), but one cooperative launch per sweep: CTA r keeps vectors
+// [r L, (r + 1) L) of the state (and, backward, of the adjoint) in shared
+// memory for all K iterations, and the per-iteration sums over all N
+// amplitudes meet through grid_exchange.cuh (exact integer limbs, an arrival
+// counter, bounded waits).
+// Every CTA also keeps a replica of the M <= 256 marked amplitudes and applies
+// to it the same operations, with the same constants and explicitly rounded
+// arithmetic, as the CTA that owns them, so the replicas stay bitwise equal to
+// the owners' values.  The marked sums the method needs (the oracle term of
+// the next mean, P, and the phi gradient's sum) are then computed in every CTA
+// without communication, and the exchange carries only the full sums: forward
+// the state sum, backward the sums of the state and of the adjoint.  Every CTA
+// forms the next pass's constants itself (FP64, the same operations in every
+// CTA, so the same values); phase factors come from a table filled before the
+// launch and are loaded while the pass before runs.
+// The backward sweep carries lambda~ = sqrt(P) lambda, whose entries are at
+// most 1 in magnitude (|lambda~_K,x| = |psi_x| / sqrt(P) <= 1 and the sweep is
+// unitary), so its sums stay inside the fixed-point window whatever P is; the
+// gradients and the stored lambda_0 are scaled back by 1 / sqrt(P).
+#include "fixed_sum.cuh"
+#include "grid_exchange.cuh"
+#include "grover_internal.cuh"
+#include "phase_ops.cuh"
+
+namespace grv {
+namespace {
+
+using ph::dcmul;
+using ph::expi;
+using ph::pairwise;
+using ph::split_hilo;
+using ph::sub_hilo;
+using ph::warp_sum_d;
+
+constexpr int kPgThreads = 512;
+constexpr int kPgWarps = kPgThreads / 32;
+constexpr int kNVmax = 4;  // sums per exchange: 2 forward, 4 backward
+constexpr int kU = 4;      // vectors per thread per group
+
+// complex product with every operation rounded on its own (no contraction),
+// so an owner and a replica compute bitwise the same value
+__device__ __forceinline__ float2 cmul_rn(float2 a, float2 b) {
+    return make_float2(__fsub_rn(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y)),
+                       __fadd_rn(__fmul_rn(a.x, b.y), __fmul_rn(a.y, b.x)));
+}
+
+// CTA reduction of NV sums, then the grid exchange by thread 0; the totals
+// land in tot (shared).  Returns false in every thread if a wait ran out (the
+// status word is set).
+// The two exchange series in the region: one of two sums (the forward sweep;
+// the backward sweep's first exchange), then one of four (the backward passes).
+__device__ __forceinline__ unsigned long long *series2(const PhaseGridArgs &a) { return a.region; }
+__device__ __forceinline__ unsigned long long *series4(const PhaseGridArgs &a) {
+    return a.region + (GxLayout<2>::kAccBytes + GxLayout<2>::side_bytes(512)) / sizeof(unsigned long long);
+}
+
+// side_job runs in warp 1 while warp 0 waits for the other CTAs (it must
+// not touch wint / wsd and must leave its results in shared memory).
+template <int NV, class Job>
+__device__ bool cta_exchange(u128 (&v)[NV], double (&sd)[NV], const PhaseGridArgs &a, unsigned long long *region,
+                             long long xi, unsigned long long (&prev)[2][3 * NV + 1], double *tot, bool withhold,
+                             Job side_job) {
+    __shared__ unsigned long long wint[kPgWarps][kNVmax][2];
+    __shared__ double wsd[kPgWarps][kNVmax];
+    __shared__ int s_ok;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int local_side = 0;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        v[q] = warp_sum_u128(v[q]);
+        local_side |= (sd[q] != 0.0);
+    }
+    const int any_side = __syncthreads_or(local_side);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        if (any_side) sd[q] = warp_sum_d(sd[q]);
+        if (lane == 0) {
+            wint[warp][q][0] = (unsigned long long)v[q];
+            wint[warp][q][1] = (unsigned long long)(v[q] >> 64);
+            wsd[warp][q] = sd[q];
+        }
+    }
+    __syncthreads();
+    if (warp == 1) side_job();
+    if (warp == 0) {
+        u128 t[NV];
+        double ts[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            t[q] = 0;
+            ts[q] = 0.0;
+            if (lane < kPgWarps) {
+                t[q] = ((u128)wint[lane][q][1] << 64) | wint[lane][q][0];
+                ts[q] = wsd[lane][q];
+            }
+            t[q] = warp_sum_u128(t[q]);
+            if (any_side) ts[q] = warp_sum_d(ts[q]);
+        }
+        if (lane == 0) {
+            double out[NV];
+            const bool ok = gx_exchange<NV>(t, ts, any_side, region, prev, xi, gridDim.x, blockIdx.x, a.wait_limit,
+                                            withhold, out);
+            if (ok) {
+#pragma unroll
+                for (int q = 0; q < NV; ++q) tot[q] = out[q];
+            } else {
+                atomicExch(a.status, 3);
+            }
+            s_ok = ok;
+        }
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Marked bitmask of this CTA's slice (amplitudes [a0, a0 + nbits)) in shared memory.
+__device__ void build_mask(uint32_t *fm, uint32_t nwords, const PhaseGridArgs &a, uint64_t a0, uint32_t nbits) {
+    for (uint32_t w = threadIdx.x; w < nwords; w += kPgThreads) fm[w] = 0u;
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < a.m; i += kPgThreads) {
+        const uint64_t x = a.list[i];
+        if (x >= a0 && x < a0 + nbits) atomicOr(fm + ((x - a0) >> 5), 1u << (uint32_t)((x - a0) & 31));
+    }
+    __syncthreads();
+}
+
+// e^{i phi_t} and e^{i vphi_t}: from the table the launcher filled, else
+// computed here
+struct Fac {
+    double2 e, ev;
+};
+__device__ __forceinline__ Fac factors(const PhaseGridArgs &a, long long t) {
+    if (a.table) return Fac{__ldg(a.table + 2 * t), __ldg(a.table + 2 * t + 1)};
+    return Fac{expi(a.phi[t]), expi(a.vphi[t])};
+}
+
+__global__ void k_phase_table(const double *phi, const double *vphi, long long K, double2 *table) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= K) return;
+    table[2 * t] = expi(phi[t]);
+    table[2 * t + 1] = expi(vphi[t]);
+}
+
+__device__ __forceinline__ uint32_t mark2(const uint32_t *fm, uint32_t j) {
+    const uint32_t e = 2 * j;
+    return (fm[e >> 5] >> (e & 31)) & 3u;
+}
+
+// Warp 1 sums the replica: out = (sum Re, sum Im, sum |c|^2) in FP64 from
+// exact fixed-point sums (the same value in every CTA).
+__device__ void replica_sums(const float2 *rep, uint32_t m, double *out) {
+    if ((threadIdx.x >> 5) != 1) return;
+    const int lane = threadIdx.x & 31;
+    u128 r = 0, i = 0, p = 0;
+    double sr = 0.0, si = 0.0, sp = 0.0;
+    for (uint32_t q = lane; q < m; q += 32) {
+        const float2 c = rep[q];
+        fix_add<4>(r, sr, c.x);
+        fix_add<4>(i, si, c.y);
+        fix_add<4>(p, sp, (double)c.x * c.x + (double)c.y * c.y);
+    }
+    r = warp_sum_u128(r);
+    i = warp_sum_u128(i);
+    p = warp_sum_u128(p);
+    sr = warp_sum_d(sr);
+    si = warp_sum_d(si);
+    sp = warp_sum_d(sp);
+    if (lane == 0) {
+        out[0] = i192_to_double(i192_from(r)) * 0x1p-100 + sr;
+        out[1] = i192_to_double(i192_from(i)) * 0x1p-100 + si;
+        out[2] = i192_to_double(i192_from(p)) * 0x1p-100 + sp;
+    }
+}
+
+// ---- forward sweep -----------------------------------------------------------
+__global__ void __launch_bounds__(kPgThreads, 1) k_phase_grid_fwd(PhaseGridArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double tot[2], rs[3];
+    __shared__ float4 s_kap;
+    __shared__ float2 s_rot;
+    __shared__ float2 rep[kPhaseMaxMarked];
+    __shared__ unsigned long long prev[2][3 * 2 + 1];
+    const unsigned rank = blockIdx.x;
+    float4 *sl = reinterpret_cast<float4 *>(smem);
+    const uint64_t start = (uint64_t)rank * a.slice_vecs;
+    const uint32_t nv = start >= a.nvec ? 0u
+                        : (uint32_t)((a.nvec - start) < a.slice_vecs ? (a.nvec - start) : a.slice_vecs);
+    uint32_t *fm = reinterpret_cast<uint32_t *>(smem + (size_t)a.slice_vecs * 16);
+    const uint32_t nwords = (a.slice_vecs * 2 + 31) / 32;
+    float4 *g = static_cast<float4 *>(a.psi) + start;
+    const float2 *g2 = static_cast<const float2 *>(a.psi);
+    for (uint32_t j = threadIdx.x; j < nv; j += kPgThreads) sl[j] = g[j];
+    for (uint32_t q = threadIdx.x; q < a.m; q += kPgThreads) rep[q] = g2[a.list[q]];
+    if (threadIdx.x < 2 * 7) prev[threadIdx.x / 7][threadIdx.x % 7] = 0ull;
+    build_mask(fm, nwords, a, start * 2, nv * 2);
+    const double inv_n = ldexp(1.0, -a.n);
+    bool ok = true;
+    for (long long t = -1; t < a.K && ok; ++t) {
+        const bool upd = t >= 0;
+        float4 kap = make_float4(0.f, 0.f, 0.f, 0.f);
+        float2 rot = make_float2(1.f, 0.f);
+        if (upd) {
+            kap = s_kap;
+            rot = s_rot;
+        }
+        // the next pass's phase factors, loaded while this pass runs
+        Fac fac{make_double2(1.0, 0.0), make_double2(1.0, 0.0)};
+        if (threadIdx.x == 0 && t + 1 < a.K) fac = factors(a, t + 1);
+        u128 v[2] = {0, 0};
+        double sd[2] = {0.0, 0.0};
+        for (uint32_t j0 = threadIdx.x; j0 < nv; j0 += kU * kPgThreads) {
+            float gr[2 * kU], gi[2 * kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const uint32_t j = j0 + u * kPgThreads;
+                if (j >= nv) {
+                    gr[2 * u] = gr[2 * u + 1] = gi[2 * u] = gi[2 * u + 1] = 0.f;
+                    continue;
+                }
+                const float4 c = sl[j];
+                float2 c0 = make_float2(c.x, c.y), c1 = make_float2(c.z, c.w);
+                if (upd) {
+                    const uint32_t f = mark2(fm, j);
+                    if (f & 1u) c0 = cmul_rn(c0, rot);
+                    if (f & 2u) c1 = cmul_rn(c1, rot);
+                    c0 = sub_hilo(c0, kap);
+                    c1 = sub_hilo(c1, kap);
+                    sl[j] = make_float4(c0.x, c0.y, c1.x, c1.y);
+                }
+                gr[2 * u] = c0.x;
+                gi[2 * u] = c0.y;
+                gr[2 * u + 1] = c1.x;
+                gi[2 * u + 1] = c1.y;
+            }
+            fix_add<4>(v[0], sd[0], pairwise<2 * kU>(gr));
+            fix_add<4>(v[1], sd[1], pairwise<2 * kU>(gi));
+        }
+        const bool withhold = a.stall && t == -1 && rank == 0;
+        // while the exchange waits: the replica of the marked amplitudes goes
+        // through the same update, and its sums are taken
+        auto job = [&]() {
+            if (upd)
+                for (uint32_t q = threadIdx.x & 31; q < a.m; q += 32) rep[q] = sub_hilo(cmul_rn(rep[q], rot), kap);
+            __syncwarp();
+            replica_sums(rep, a.m, rs);
+        };
+        ok = cta_exchange<2>(v, sd, a, series2(a), t + 1, prev, tot, withhold, job);
+        if (!ok) break;
+        if (threadIdx.x == 0) {
+            const long long nxt = t + 1;
+            if (nxt < a.K) {
+                // mean of O(phi_{t+1}) c: S + (e^{i phi} - 1) A, over N
+                const double2 e = fac.e, ev = fac.ev;
+                const double cr = (e.x - 1.0) * rs[0] - e.y * rs[1];
+                const double ci = (e.x - 1.0) * rs[1] + e.y * rs[0];
+                const double2 mu = make_double2((tot[0] + cr) * inv_n, (tot[1] + ci) * inv_n);
+                s_kap = split_hilo(dcmul(make_double2(1.0 - ev.x, -ev.y), mu));
+                s_rot = make_float2((float)e.x, (float)e.y);
+            } else if (rank == 0 && a.stats) {
+                a.stats[0] = rs[2];
+                a.stats[1] = -log(rs[2]);
+            }
+        }
+        __syncthreads();
+    }
+    for (uint32_t j = threadIdx.x; j < nv; j += kPgThreads) g[j] = sl[j];
+}
+
+// ---- backward sweep ----------------------------------------------------------
+__global__ void __launch_bounds__(kPgThreads, 1) k_phase_grid_bwd(PhaseGridArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double tot[4], rs[3];
+    __shared__ float4 s_kp, s_kl;
+    __shared__ float2 s_rot;
+    __shared__ double s_is, s_g;
+    __shared__ float2 repp[kPhaseMaxMarked], repl[kPhaseMaxMarked];
+    __shared__ unsigned long long prev2[2][3 * 2 + 1], prev4[2][3 * 4 + 1];
+    const unsigned rank = blockIdx.x;
+    float4 *sp = reinterpret_cast<float4 *>(smem);
+    float4 *sm = sp + a.slice_vecs;
+    const uint64_t start = (uint64_t)rank * a.slice_vecs;
+    const uint32_t nv = start >= a.nvec ? 0u
+                        : (uint32_t)((a.nvec - start) < a.slice_vecs ? (a.nvec - start) : a.slice_vecs);
+    uint32_t *fm = reinterpret_cast<uint32_t *>(smem + (size_t)a.slice_vecs * 32);
+    const uint32_t nwords = (a.slice_vecs * 2 + 31) / 32;
+    float4 *gp = static_cast<float4 *>(a.psi) + start;
+    float4 *gl = static_cast<float4 *>(a.lam) + start;
+    const float2 *g2 = static_cast<const float2 *>(a.psi);
+    for (uint32_t j = threadIdx.x; j < nv; j += kPgThreads) sp[j] = gp[j];
+    for (uint32_t q = threadIdx.x; q < a.m; q += kPgThreads) repp[q] = g2[a.list[q]];
+    if (threadIdx.x < 2 * 7) prev2[threadIdx.x / 7][threadIdx.x % 7] = 0ull;
+    if (threadIdx.x < 2 * 13) prev4[threadIdx.x / 13][threadIdx.x % 13] = 0ull;
+    build_mask(fm, nwords, a, start * 2, nv * 2);
+    const double N = ldexp(1.0, a.n), inv_n = ldexp(1.0, -a.n);
+    // P from the replica (every CTA), lambda~_K = -(marked psi_K) / sqrt(P)
+    replica_sums(repp, a.m, rs);
+    __syncthreads();
+    if (threadIdx.x == 0) s_is = 1.0 / sqrt(rs[2]);
+    __syncthreads();
+    const double is = s_is;
+    for (uint32_t q = threadIdx.x; q < a.m; q += kPgThreads)
+        repl[q] = make_float2((float)(-(double)repp[q].x * is), (float)(-(double)repp[q].y * is));
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < nv; j += kPgThreads) {
+        const uint32_t f = mark2(fm, j);
+        float4 l = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (f) {
+            const float4 c = sp[j];
+            if (f & 1u) {
+                l.x = (float)(-(double)c.x * is);
+                l.y = (float)(-(double)c.y * is);
+            }
+            if (f & 2u) {
+                l.z = (float)(-(double)c.z * is);
+                l.w = (float)(-(double)c.w * is);
+            }
+        }
+        sm[j] = l;
+    }
+    // exchange 0: the sum of psi_K (the adjoint's sum is the replica's)
+    bool ok;
+    {
+        u128 v[2] = {0, 0};
+        double sd[2] = {0.0, 0.0};
+        for (uint32_t j0 = threadIdx.x; j0 < nv; j0 += kU * kPgThreads) {
+            float gr[2 * kU], gi[2 * kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const uint32_t j = j0 + u * kPgThreads;
+                if (j >= nv) {
+                    gr[2 * u] = gr[2 * u + 1] = gi[2 * u] = gi[2 * u + 1] = 0.f;
+                    continue;
+                }
+                const float4 c = sp[j];
+                gr[2 * u] = c.x;
+                gi[2 * u] = c.y;
+                gr[2 * u + 1] = c.z;
+                gi[2 * u + 1] = c.w;
+            }
+            fix_add<4>(v[0], sd[0], pairwise<2 * kU>(gr));
+            fix_add<4>(v[1], sd[1], pairwise<2 * kU>(gi));
+        }
+        ok = cta_exchange<2>(v, sd, a, series2(a), 0, prev2, tot, a.stall && rank == 0,
+                             [&]() { replica_sums(repl, a.m, rs); });
+    }
+    if (ok && threadIdx.x == 0 && a.K > 0) {
+        const double2 mp = make_double2(tot[0] * inv_n, tot[1] * inv_n);
+        const double2 ml = make_double2(rs[0] * inv_n, rs[1] * inv_n);
+        if (rank == 0) a.grad_vphi[a.K - 1] = -2.0 * N * (ml.x * mp.y - ml.y * mp.x) * is;
+        const Fac f = factors(a, a.K - 1);  // conjugates: e^{-i phi}, e^{-i vphi}
+        const double2 ev = make_double2(f.ev.x, -f.ev.y), e = make_double2(f.e.x, -f.e.y);
+        const double2 one_m = make_double2(1.0 - ev.x, -ev.y);
+        s_kp = split_hilo(dcmul(one_m, mp));
+        s_kl = split_hilo(dcmul(one_m, ml));
+        s_rot = make_float2((float)e.x, (float)e.y);
+    }
+    __syncthreads();
+    // ---- the K adjoint passes (exchanges 1..K of the second counter series) ----
+    long long xi = 0;
+    for (long long t = a.K - 1; t >= 0 && ok; --t, ++xi) {
+        const float4 kp = s_kp, kl = s_kl;
+        const float2 rot = s_rot;
+        Fac fac{make_double2(1.0, 0.0), make_double2(1.0, 0.0)};
+        if (threadIdx.x == 0 && t > 0) fac = factors(a, t - 1);
+        u128 v[4] = {0, 0, 0, 0};
+        double sd[4] = {0.0, 0.0, 0.0, 0.0};
+        for (uint32_t j0 = threadIdx.x; j0 < nv; j0 += kU * kPgThreads) {
+            float pr[2 * kU], pi[2 * kU], lr[2 * kU], li[2 * kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const uint32_t j = j0 + u * kPgThreads;
+                if (j >= nv) {
+                    pr[2 * u] = pr[2 * u + 1] = pi[2 * u] = pi[2 * u + 1] = 0.f;
+                    lr[2 * u] = lr[2 * u + 1] = li[2 * u] = li[2 * u + 1] = 0.f;
+                    continue;
+                }
+                const float4 c = sp[j], l = sm[j];
+                const uint32_t f = mark2(fm, j);
+                float2 c0 = sub_hilo(make_float2(c.x, c.y), kp), c1 = sub_hilo(make_float2(c.z, c.w), kp);
+                float2 l0 = sub_hilo(make_float2(l.x, l.y), kl), l1 = sub_hilo(make_float2(l.z, l.w), kl);
+                if (f & 1u) {
+                    c0 = cmul_rn(c0, rot);
+                    l0 = cmul_rn(l0, rot);
+                }
+                if (f & 2u) {
+                    c1 = cmul_rn(c1, rot);
+                    l1 = cmul_rn(l1, rot);
+                }
+                sp[j] = make_float4(c0.x, c0.y, c1.x, c1.y);
+                sm[j] = make_float4(l0.x, l0.y, l1.x, l1.y);
+                pr[2 * u] = c0.x;
+                pi[2 * u] = c0.y;
+                pr[2 * u + 1] = c1.x;
+                pi[2 * u + 1] = c1.y;
+                lr[2 * u] = l0.x;
+                li[2 * u] = l0.y;
+                lr[2 * u + 1] = l1.x;
+                li[2 * u + 1] = l1.y;
+            }
+            fix_add<4>(v[0], sd[0], pairwise<2 * kU>(pr));
+            fix_add<4>(v[1], sd[1], pairwise<2 * kU>(pi));
+            fix_add<4>(v[2], sd[2], pairwise<2 * kU>(lr));
+            fix_add<4>(v[3], sd[3], pairwise<2 * kU>(li));
+        }
+        // while the exchange waits: replicas of psi and lambda~ on the marked
+        // set, and the phi gradient's sum sum_marked Im(conj(lambda~) psi)
+        auto job = [&]() {
+            u128 gs = 0;
+            double gsd = 0.0;
+            for (uint32_t q = threadIdx.x & 31; q < a.m; q += 32) {
+                const float2 c = cmul_rn(sub_hilo(repp[q], kp), rot), l = cmul_rn(sub_hilo(repl[q], kl), rot);
+                repp[q] = c;
+                repl[q] = l;
+                fix_add<4>(gs, gsd, (double)l.x * c.y - (double)l.y * c.x);
+            }
+            gs = warp_sum_u128(gs);
+            gsd = warp_sum_d(gsd);
+            if ((threadIdx.x & 31) == 0) s_g = i192_to_double(i192_from(gs)) * 0x1p-100 + gsd;
+        };
+        ok = cta_exchange<4>(v, sd, a, series4(a), xi, prev4, tot, false, job);
+        if (!ok) break;
+        if (threadIdx.x == 0) {
+            const double2 mp = make_double2(tot[0] * inv_n, tot[1] * inv_n);
+            const double2 ml = make_double2(tot[2] * inv_n, tot[3] * inv_n);
+            if (rank == 0) {
+                // dL/dphi_t = -2 Im(sum_marked conj(lambda_t) psi_t)
+                a.grad_phi[t] = -2.0 * s_g * is;
+                // dL/dvphi_{t-1} = -2 N Im(conj(<lambda_t>) <psi_t>)
+                if (t > 0) a.grad_vphi[t - 1] = -2.0 * N * (ml.x * mp.y - ml.y * mp.x) * is;
+            }
+            if (t > 0) {
+                const double2 ev = make_double2(fac.ev.x, -fac.ev.y), e = make_double2(fac.e.x, -fac.e.y);
+                const double2 one_m = make_double2(1.0 - ev.x, -ev.y);
+                s_kp = split_hilo(dcmul(one_m, mp));
+                s_kl = split_hilo(dcmul(one_m, ml));
+                s_rot = make_float2((float)e.x, (float)e.y);
+            }
+        }
+        __syncthreads();
+    }
+    // psi_0 (rewound) and lambda_0 = lambda~_0 / sqrt(P); after a wait that
+    // ran out the results are undefined and lambda is left as it was
+    for (uint32_t j = threadIdx.x; j < nv; j += kPgThreads) gp[j] = sp[j];
+    if (ok) {
+        for (uint32_t j = threadIdx.x; j < nv; j += kPgThreads) {
+            const float4 l = sm[j];
+            gl[j] = make_float4((float)(l.x * is), (float)(l.y * is), (float)(l.z * is), (float)(l.w * is));
+        }
+    }
+}
+
+template <class F> cudaError_t launch_coop(F kern, unsigned G, size_t smem, cudaStream_t st, const PhaseGridArgs &a,
+                                           size_t *smem_set) {
+    cudaError_t e;
+    if (smem > *smem_set) {
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+            return e;
+        *smem_set = smem;
+    }
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPgThreads, smem)) != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorNotSupported;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(G);
+    cfg.blockDim = dim3(kPgThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;  // all G CTAs co-resident, or the launch fails
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+}  // namespace
+
+bool phase_grid_plan(int n, bool backward, int sm_count, unsigned *G, uint32_t *slice_vecs, size_t *smem) {
+    const uint64_t nvec = (1ull << n) / 2;
+    if (n < 2 || sm_count < 1 || sm_count > 512 || nvec < (uint64_t)sm_count) return false;
+    const uint64_t L = (nvec + sm_count - 1) / sm_count;
+    const size_t bytes = (size_t)L * 16 * (backward ? 2 : 1) + ((L * 2 + 31) / 32) * 4;
+    if (bytes > kPhaseGridSmemMax) return false;
+    *G = (unsigned)((nvec + L - 1) / L);
+    *slice_vecs = (uint32_t)L;
+    *smem = bytes;
+    return true;
+}
+
+// Two exchange series: one of two sums (the forward sweep; the backward
+// sweep's first exchange), one of four (the backward passes).
+size_t phase_grid_region_bytes(unsigned G) {
+    return GxLayout<2>::kAccBytes + GxLayout<2>::side_bytes(G) + GxLayout<4>::kAccBytes + GxLayout<4>::side_bytes(G);
+}
+size_t phase_grid_zero_bytes() { return phase_grid_region_bytes(512); }
+
+cudaError_t launch_phase_table(const double *phi, const double *vphi, long long K, double2 *table, cudaStream_t st) {
+    if (K <= 0) return cudaSuccess;
+    k_phase_table<<<(unsigned)((K + 255) / 256), 256, 0, st>>>(phi, vphi, K, table);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_phase_grid(const PhaseGridArgs &a, bool backward, unsigned G, size_t smem, cudaStream_t st) {
+    static size_t set_f = 0, set_b = 0;
+    if (backward) return launch_coop(k_phase_grid_bwd, G, smem, st, a, &set_b);
+    return launch_coop(k_phase_grid_fwd, G, smem, st, a, &set_f);
+}
+
+}  // namespace grv

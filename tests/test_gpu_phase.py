@@ -54,8 +54,12 @@ def dev(x):
     return torch.as_tensor(np.asarray(x, dtype=np.float64), device="cuda").contiguous()
 
 
-def run_forward(B, n, marked, phi, vphi, init=None):
+PATHS = {"auto": -1, "pass": 0}
+
+
+def run_forward(B, n, marked, phi, vphi, init=None, path="auto"):
     st = B.State(n, "c64")
+    st.set_resident(PATHS[path])
     mk = B.Marked(n, marked)
     if init is None:
         st.init_uniform()
@@ -101,10 +105,11 @@ def c64_start(n, seed):
 
 # ---- forward ----------------------------------------------------------------------
 @pytest.mark.parametrize("n,m,K", [(3, 1, 5), (12, 1, 50), (12, 4, 25), (17, 2, 40)])
-def test_pi_is_minus_grover(B, n, m, K):
+@pytest.mark.parametrize("path", ["auto", "pass"])
+def test_pi_is_minus_grover(B, n, m, K, path):
     marked = inputs.marked_indices(n, m, seed=700 + n)
     phi = np.full(K, np.pi)
-    st, _, stats = run_forward(B, n, marked, phi, phi)
+    st, _, stats = run_forward(B, n, marked, phi, phi, path=path)
     got = amps(st)
     ref = oracle.init_uniform(n)
     oracle.grover_operator(ref, n, marked, K)
@@ -117,11 +122,12 @@ def test_pi_is_minus_grover(B, n, m, K):
 
 @pytest.mark.parametrize("n,m,K", [(1, 1, 3), (2, 1, 4), (3, 2, 7), (5, 32, 6), (9, 5, 10), (14, 3, 20),
                                    (14, 256, 8), (16, 1, 12)])
-def test_forward_matches_oracle(B, n, m, K):
+@pytest.mark.parametrize("path", ["auto", "pass"])
+def test_forward_matches_oracle(B, n, m, K, path):
     marked = inputs.marked_indices(n, m, seed=710 + n + m)
     phi, vphi = inputs.uniform_phases(K, seed=720 + n)
     psi0 = c64_start(n, seed=730 + n)
-    st, _, stats = run_forward(B, n, marked, phi, vphi, init=psi0)
+    st, _, stats = run_forward(B, n, marked, phi, vphi, init=psi0, path=path)
     got = amps(st)
     ref = psi0.copy()
     oracle.phase_grover(ref, n, marked, phi, vphi)
@@ -134,24 +140,26 @@ def test_forward_matches_oracle(B, n, m, K):
     assert abs(stats[1] - L_ref) <= 1.01 * p_tol(K, A, P_ref, m) / P_ref
 
 
-def test_forward_k0_is_loss_of_start(B):
+@pytest.mark.parametrize("path", ["auto", "pass"])
+def test_forward_k0_is_loss_of_start(B, path):
     n, K = 10, 0
     marked = inputs.marked_indices(n, 3, seed=740)
     psi0 = c64_start(n, seed=741)
-    st, _, stats = run_forward(B, n, marked, [], [], init=psi0)
+    st, _, stats = run_forward(B, n, marked, [], [], init=psi0, path=path)
     assert np.array_equal(amps(st), psi0)
     p = float(np.sum(np.abs(psi0[marked.astype(np.int64)]) ** 2))
     assert abs(stats[0] - p) <= 1e-12 * max(p, 1.0)
     assert abs(stats[1] + math.log(p)) <= 1e-10
 
 
-def test_uniform_n20_matches_reduced_model(B):
+@pytest.mark.parametrize("path", ["auto", "pass"])
+def test_uniform_n20_matches_reduced_model(B, path):
     """Config: n = 20, M = 3, K = 32, phases U(0, 2 pi): loss and the two
     amplitudes against the exact FP64 reduced model."""
     n, m, K = 20, 3, 32
     marked = inputs.marked_indices(n, m, seed=750)
     phi, vphi = inputs.uniform_phases(K, seed=751)
-    st, _, stats = run_forward(B, n, marked, phi, vphi)
+    st, _, stats = run_forward(B, n, marked, phi, vphi, path=path)
     L_ref, alpha, beta = oracle.phase_reduced(n, m, phi, vphi)
     got = amps(st)
     mask = np.zeros(1 << n, dtype=bool)
@@ -184,11 +192,12 @@ def oracle_loss_fn(n, marked, psi0):
 
 
 @pytest.mark.parametrize("n,m,K", [(2, 1, 3), (6, 3, 8), (12, 2, 12), (13, 7, 10)])
-def test_gradients_match_oracle_fd(B, n, m, K):
+@pytest.mark.parametrize("path", ["auto", "pass"])
+def test_gradients_match_oracle_fd(B, n, m, K, path):
     marked = inputs.marked_indices(n, m, seed=760 + n)
     phi, vphi = inputs.uniform_phases(K, seed=761 + n)
     psi0 = c64_start(n, seed=762 + n)
-    st, mk, _ = run_forward(B, n, marked, phi, vphi, init=psi0)
+    st, mk, _ = run_forward(B, n, marked, phi, vphi, init=psi0, path=path)
     gp, gv, _ = run_backward(B, st, mk, phi, vphi)
     fp, fv = oracle.phase_grad_fd(oracle_loss_fn(n, marked, psi0), phi, vphi, h=1e-6)
     scale = max(np.max(np.abs(fp)), np.max(np.abs(fv)))
@@ -201,14 +210,15 @@ def test_gradients_match_oracle_fd(B, n, m, K):
     assert np.max(np.abs(back - psi0)) <= 2 * state_tol(K, A)
 
 
-def test_config_n20_gradients(B):
+@pytest.mark.parametrize("path", ["auto", "pass"])
+def test_config_n20_gradients(B, path):
     """n = 20, M = 3, K = 32, uniform start: adjoint gradients against the FP64
     reduced model (central differences, h = 1e-6) and against central
     differences of the GPU loss (h = 1e-4)."""
     n, m, K = 20, 3, 32
     marked = inputs.marked_indices(n, m, seed=750)
     phi, vphi = inputs.uniform_phases(K, seed=751)
-    st, mk, stats = run_forward(B, n, marked, phi, vphi)
+    st, mk, stats = run_forward(B, n, marked, phi, vphi, path=path)
     gp, gv, lam = run_backward(B, st, mk, phi, vphi)
     fp, fv = oracle.phase_grad_fd(lambda a, b: oracle.phase_reduced(n, m, a, b)[0], phi, vphi, h=1e-6)
     scale = max(np.max(np.abs(fp)), np.max(np.abs(fv)))
@@ -216,6 +226,7 @@ def test_config_n20_gradients(B):
     assert np.max(np.abs(gv - fv)) <= 2e-4 * scale
     # central differences of the GPU loss at a few components
     st2 = B.State(n, "c64")
+    st2.set_resident(PATHS[path])
     stats2 = torch.zeros(2, dtype=torch.float64, device="cuda")
 
     def gpu_loss(a, b):
@@ -237,13 +248,14 @@ def test_config_n20_gradients(B):
             assert abs(d - g[t]) <= 2e-2 * scale, (t, d, g[t])
 
 
-def test_lambda0_gives_directional_derivatives(B):
+@pytest.mark.parametrize("path", ["auto", "pass"])
+def test_lambda0_gives_directional_derivatives(B, path):
     """dL along a direction delta of the initial state is 2 Re <lambda_0, delta>."""
     n, m, K = 11, 4, 9
     marked = inputs.marked_indices(n, m, seed=770)
     phi, vphi = inputs.uniform_phases(K, seed=771)
     psi0 = c64_start(n, seed=772)
-    st, mk, _ = run_forward(B, n, marked, phi, vphi, init=psi0)
+    st, mk, _ = run_forward(B, n, marked, phi, vphi, init=psi0, path=path)
     _, _, lam = run_backward(B, st, mk, phi, vphi)
     f = oracle_loss_fn(n, marked, psi0)
     for s in range(3):
@@ -262,11 +274,12 @@ def test_lambda0_gives_directional_derivatives(B):
     assert f(phi, vphi) > 0
 
 
-def test_backward_k0(B):
+@pytest.mark.parametrize("path", ["auto", "pass"])
+def test_backward_k0(B, path):
     n = 9
     marked = inputs.marked_indices(n, 2, seed=780)
     psi0 = c64_start(n, seed=781)
-    st, mk, _ = run_forward(B, n, marked, [], [], init=psi0)
+    st, mk, _ = run_forward(B, n, marked, [], [], init=psi0, path=path)
     gp, gv, lam = run_backward(B, st, mk, [], [])
     assert gp.size == 0 and gv.size == 0
     idx = marked.astype(np.int64)
@@ -340,3 +353,30 @@ def test_autograd_function_and_adam(B):
     assert math.exp(-L_ref) <= bound * (1 + 1e-9)
     # the FP64 reduced model under the same optimiser reaches 4.57 from 9.02
     assert final < first - 4.0, (first, final)
+
+
+def test_onchip_sweep_wait_runs_out(B):
+    """Failure detection without a GPU fault: CTA 0 of the on-chip forward
+    sweep withholds its first contribution (test hook), every wait runs out,
+    grover_sync reports GROVER_ETIMEOUT and the handle stays usable."""
+    n, K = 16, 4
+    marked = inputs.marked_indices(n, 2, seed=790)
+    phi, vphi = inputs.uniform_phases(K, seed=791)
+    st = B.State(n, "c64")
+    mk = B.Marked(n, marked)
+    st.set_resident(2)
+    st.set_option(2, 20000)
+    st.set_option(3, 1)
+    st.init_uniform()
+    st.phase_forward(mk, dev(phi), dev(vphi))
+    with pytest.raises(B.GroverError) as ei:
+        st.sync()
+    assert ei.value.status == 4
+    st.set_option(2, 1 << 22)
+    st.init_uniform()
+    stats = torch.zeros(2, dtype=torch.float64, device="cuda")
+    st.phase_forward(mk, dev(phi), dev(vphi), stats)
+    st.sync()
+    psi = oracle.init_uniform(n)
+    oracle.phase_grover(psi, n, marked, phi, vphi)
+    assert abs(float(stats[1]) - oracle.phase_loss(psi, n, marked)) <= 1e-4
