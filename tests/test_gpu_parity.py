@@ -424,3 +424,24 @@ def test_resident_grid_wait_runs_out(B):
     st.sync()
     a_m, _ = oracle.closed_form_uniform(n, 2, k)
     assert abs(to_np(st)[int(marked[0])] - a_m) <= 3 * k * 2.0 ** -24
+
+
+# ---- amplitudes outside the fixed-point window ----------------------------------------------
+@pytest.mark.parametrize("path,n", [("pass", 14), ("cluster", 12), ("grid", 18)])
+def test_out_of_window_amplitudes(B, path, n):
+    """A state scaled by 64 (amplitudes above the 16 of the exact fixed-point
+    window) takes the FP64 side sums in every reduction; the iterator is linear,
+    so the result is 64 times the unit-norm one."""
+    m, k = 3, 7
+    marked = inputs.marked_indices(n, m, seed=900 + n)
+    psi0 = inputs.gaussian_state(n, seed=901 + n)
+    psi0[int(marked[0])] = 0.9  # one large amplitude, so the scaled state has values >= 16
+    psi0 = psi0.astype(np.complex64).astype(np.complex128)
+    scaled = (psi0 * 64.0).astype(np.complex64).astype(np.complex128)
+    st = B.State(n, "c64")
+    st.set_resident({"pass": 0, "cluster": 1, "grid": 2}[path])
+    st.init_state(scaled)
+    st.iterate(B.Marked(n, marked), k)
+    st.sync()
+    ref = oracle.grover_operator(scaled.copy(), n, marked, k)
+    assert np.max(np.abs(to_np(st) - ref)) <= 64.0 * 2.0 * c64_tol(k)

@@ -380,3 +380,31 @@ def test_onchip_sweep_wait_runs_out(B):
     psi = oracle.init_uniform(n)
     oracle.phase_grover(psi, n, marked, phi, vphi)
     assert abs(float(stats[1]) - oracle.phase_loss(psi, n, marked)) <= 1e-4
+
+
+@pytest.mark.parametrize("path", ["auto", "pass"])
+def test_scaled_start_takes_side_sums(B, path):
+    """A start scaled by 64 puts amplitudes outside the fixed-point window (the
+    FP64 side sums of every reduction, and on chip the side slots of the grid
+    exchange); the loss shifts by -log(64^2) and the gradients are unchanged."""
+    n, m, K = 15, 3, 6
+    marked = inputs.marked_indices(n, m, seed=795)
+    phi, vphi = inputs.uniform_phases(K, seed=796)
+    psi0 = c64_start(n, seed=797)
+    psi0[int(marked[0])] = 0.9
+    psi0 = psi0.astype(np.complex64).astype(np.complex128)
+    scaled = (psi0 * 64.0).astype(np.complex64).astype(np.complex128)
+    st, mk, stats = run_forward(B, n, marked, phi, vphi, init=scaled, path=path)
+    ref = scaled.copy()
+    oracle.phase_grover(ref, n, marked, phi, vphi)
+    A = oracle_traj_max(n, marked, phi, vphi, scaled)
+    assert np.max(np.abs(amps(st) - ref)) <= state_tol(K, A)
+    L_ref = oracle.phase_loss(ref, n, marked)
+    assert abs(stats[1] - L_ref) <= 1e-4
+    gp, gv, _ = run_backward(B, st, mk, phi, vphi)
+    fp, fv = oracle.phase_grad_fd(oracle_loss_fn(n, marked, psi0), phi, vphi, h=1e-6)
+    # here P ~ 0.8 and the gradients are small (~1e-4), so the bound is absolute:
+    # |dL/dphi| <= 2 and |dL/dvphi| <= 2 / sqrt(P) for a unit-norm start, and the
+    # recomputed states carry (K + 1) 2^-20 of relative error
+    tol = (K + 1) * 2.0 ** -20 * 2.0 / math.sqrt(math.exp(-L_ref) / 64.0 ** 2)
+    assert np.max(np.abs(gp - fp)) <= tol and np.max(np.abs(gv - fv)) <= tol
