@@ -46,7 +46,6 @@ namespace grv {
 namespace {
 
 constexpr int kTcThreads = 512;
-constexpr int kTcWarps = kTcThreads / 32;
 constexpr int kCols = 128;          // real columns per tile (= MMA M or N)
 constexpr uint32_t kTmemCols = 512; // three accumulators of up to 128 columns
 
@@ -133,12 +132,22 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t pari
     return done != 0;
 }
 
-// Tile geometry: first amplitude and the amplitude stride between mids.
+// Real columns of a tile: 128 for the lowest group (64 blocks x re/im); for an
+// upper group 128 x 128 / K, so every tile holds 8192 amplitudes (64 KiB) and
+// a K < 128 pass runs 128 / K column blocks of 128 through the MMAs.
+template <int KB, bool LOW> __host__ __device__ constexpr int tile_cols() { return LOW ? kCols : kCols * (128 >> KB); }
+// box width (floats) of one tensor copy of an upper-group tile (at most 256)
+template <int KB> __host__ __device__ constexpr int box_cols() {
+    return tile_cols<KB, false>() < 256 ? tile_cols<KB, false>() : 256;
+}
+
+// Tile geometry: first amplitude of the tile (the mids are 2^lo apart).
 template <int KB, bool LOW> __device__ __forceinline__ uint64_t tile_base(uint64_t tile, int lo) {
     constexpr int K = 1 << KB;
     if (LOW) return tile * (uint64_t)(kCols / 2) * K;  // 64 blocks of K amplitudes
-    const uint64_t chunks = (1ull << lo) / (kCols / 2);
-    return ((tile / chunks) << (lo + KB)) | ((tile % chunks) * (kCols / 2));
+    constexpr int AMPS = tile_cols<KB, false>() / 2;
+    const uint64_t chunks = (1ull << lo) / AMPS;
+    return ((tile / chunks) << (lo + KB)) | ((tile % chunks) * AMPS);
 }
 
 // Warp 0 streams one tile of fp32 amplitudes into the staging buffer: the
@@ -147,8 +156,7 @@ template <int KB, bool LOW>
 __device__ __forceinline__ void issue_tile_load(const float *amps, const CUtensorMap *tmap, uint64_t tile, int lo,
                                                 unsigned char *stage, unsigned long long *bar, int lane) {
     constexpr int K = 1 << KB;
-    constexpr uint32_t ROWB = (kCols / 2) * 8;  // 512 bytes: 64 complex64
-    constexpr uint32_t TILEB = (uint32_t)K * ROWB;
+    constexpr uint32_t TILEB = (uint32_t)K * tile_cols<KB, LOW>() * 4;  // 64 KiB
     const uint64_t abase = tile_base<KB, LOW>(tile, lo);
     if (lane == 0)
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(TILEB) : "memory");
@@ -164,14 +172,21 @@ __device__ __forceinline__ void issue_tile_load(const float *amps, const CUtenso
                          ::"r"(su32(stage)), "l"(tmap), "r"(0), "r"(0), "r"(z), "r"(su32(bar)) : "memory");
         }
     } else if (lane == 0) {
-        // one tiled copy: box {128 floats, K mids, 1 outer} of the view
-        // [outer][mid][2^(lo+1) floats]; x = chunk * 128 floats (a multiple of
-        // 16 bytes), y = 0, z = outer
-        const uint64_t chunks = (1ull << lo) / (kCols / 2);
-        const int x = (int)((tile % chunks) * kCols), z = (int)(tile / chunks);
-        asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-                     "[%0], [%1, {%2, %3, %4}], [%5];"
-                     ::"r"(su32(stage)), "l"(tmap), "r"(x), "r"(0), "r"(z), "r"(su32(bar)) : "memory");
+        // tiled copies of box {BOX floats, K mids, 1 outer} of the view
+        // [outer][mid][2^(lo+1) floats]; x = chunk * COLS + b * BOX floats (a
+        // multiple of 16 bytes), y = 0, z = outer; copy b lands as its own
+        // [K][BOX] block of the stage
+        constexpr int COLS = tile_cols<KB, false>(), BOX = box_cols<KB>();
+        const uint64_t chunks = (1ull << lo) / (COLS / 2);
+        const int z = (int)(tile / chunks);
+#pragma unroll
+        for (int b = 0; b < COLS / BOX; ++b) {
+            const int x = (int)((tile % chunks) * COLS) + b * BOX;
+            asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+                         "[%0], [%1, {%2, %3, %4}], [%5];"
+                         ::"r"(su32(stage + (size_t)b * K * BOX * 4)), "l"(tmap), "r"(x), "r"(0), "r"(z),
+                           "r"(su32(bar)) : "memory");
+        }
     }
     (void)amps;
 }
@@ -181,12 +196,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 k_wht_tc(float *amps, const __grid_constant__ CUtensorMap tmap, int lo, uint64_t ntiles, float scale,
          int negate_but_zero, int *status, long long wait_limit, int stall) {
     constexpr int K = 1 << KB;
-    constexpr size_t STAGE = (size_t)K * (kCols / 2) * 8;  // fp32 tile
+    constexpr int COLS = tile_cols<KB, LOW>();            // real columns (operand rows)
+    constexpr int NB = COLS / kCols;                        // column blocks of 128 (MMA M)
+    constexpr size_t STAGE = (size_t)K * COLS * 4;          // fp32 tile, 64 KiB
     constexpr uint32_t SBO = sbo_of(K);
     constexpr uint32_t LBO = kLBO;
-    constexpr size_t SLICE = (size_t)(kCols / 8) * SBO;    // one bf16 slice of the tile (128 rows)
+    constexpr size_t SLICE = (size_t)(COLS / 8) * SBO;      // one bf16 slice of the tile
     constexpr int M_MMA = 128;
-    constexpr int N_MMA = LOW ? kCols : K;
+    constexpr int N_MMA = LOW ? kCols : K;                  // accumulator columns; A12 sits N_MMA after A0
     static_assert(!LOW || KB == 7, "the lowest group uses W as the 128-row operand");
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char *stage = smem;                        // fp32 tile from global
@@ -242,12 +259,13 @@ k_wht_tc(float *amps, const __grid_constant__ CUtensorMap tmap, int lo, uint64_t
     // rounding), scale, phase shift, store.
     auto epilogue = [&](uint64_t etile, uint32_t buf) {
         const uint64_t abase = tile_base<KB, LOW>(etile, lo);
-        const int lg = warp & 3, cg = warp >> 2;
-        constexpr int NCH = N_MMA / 32;
-        if (cg < NCH) {
+        const int lg = warp & 3, cw = warp >> 2;
+        constexpr int CPB = N_MMA / 32;  // 32-column chunks per column block
+        if (cw < NB * CPB) {
+            const int blk = cw / CPB, cg = cw % CPB;
             uint32_t a[32], b[32];
-            const uint32_t t0 = taddr + 256u * buf + ((uint32_t)(32 * lg) << 16) + (uint32_t)(32 * cg);
-            tmem_ld32(t0 + 128u, a);
+            const uint32_t t0 = taddr + 256u * buf + ((uint32_t)(32 * lg) << 16) + (uint32_t)(blk * 2 * N_MMA + 32 * cg);
+            tmem_ld32(t0 + (uint32_t)N_MMA, a);
             tmem_ld32(t0, b);
 #pragma unroll
             for (int j = 0; j < 32; ++j) a[j] = __float_as_uint(__uint_as_float(a[j]) + __uint_as_float(b[j]));
@@ -283,10 +301,11 @@ k_wht_tc(float *amps, const __grid_constant__ CUtensorMap tmap, int lo, uint64_t
                     __stcs(reinterpret_cast<float4 *>(amps) + a0 / 2, v);
                 }
             } else {
-                // row = column (re or im of amplitude row / 2), registers = output
+                // row = column (re or im of amplitude col / 2), registers = output
                 // mids; lanes 2l and 2l + 1 hold re and im of one amplitude: they
                 // swap halves so each stores (re, im) pairs for 16 mids
-                const uint64_t ar = abase + (uint64_t)(row >> 1);
+                const int col = kCols * blk + row;
+                const uint64_t ar = abase + (uint64_t)(col >> 1);
                 const bool odd = lane & 1;
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
@@ -346,13 +365,17 @@ k_wht_tc(float *amps, const __grid_constant__ CUtensorMap tmap, int lo, uint64_t
                 put8(xs, SLICE, 2 * o + 1, kg * 8, K, im);
             }
         } else {
-            // unit = (k-group of 8 mids, float4 column group)
-            for (int u = tid; u < (K / 8) * (kCols / 4); u += kTcThreads) {
-                const int c4 = u % (kCols / 4), kg = u / (kCols / 4);
+            // unit = (k-group of 8 mids, float4 column group); copy b of the
+            // tile holds columns [b BOX, (b + 1) BOX) as a [K][BOX] block
+            constexpr int BOX = box_cols<KB>();
+            for (int u = tid; u < (K / 8) * (COLS / 4); u += kTcThreads) {
+                const int c4 = u % (COLS / 4), kg = u / (COLS / 4);
+                const int bx = (4 * c4) / BOX, w4 = ((4 * c4) % BOX) / 4;
+                const float4 *blk4 = reinterpret_cast<const float4 *>(stage) + (size_t)bx * K * (BOX / 4);
                 float col[4][8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    const float4 c = reinterpret_cast<const float4 *>(stage)[(size_t)(kg * 8 + j) * (kCols / 4) + c4];
+                    const float4 c = blk4[(size_t)(kg * 8 + j) * (BOX / 4) + w4];
                     col[0][j] = c.x;
                     col[1][j] = c.y;
                     col[2][j] = c.z;
@@ -375,17 +398,22 @@ k_wht_tc(float *amps, const __grid_constant__ CUtensorMap tmap, int lo, uint64_t
             constexpr uint32_t idesc = idesc_bf16(M_MMA, N_MMA);
             const uint32_t tb = taddr + 256u * (it & 1u);
 #pragma unroll 1
-            for (int s = 0; s < 3; ++s) {
+            for (int blk = 0; blk < NB; ++blk) {
 #pragma unroll 1
-                for (int kk = 0; kk < K / 16; ++kk) {
-                    const uint32_t xa = su32(xs + s * SLICE) + kk * 2 * LBO;
-                    const uint32_t wa = su32(ws) + kk * 2 * LBO;
-                    const uint64_t da = LOW ? smem_desc(wa, LBO, SBO) : smem_desc(xa, LBO, SBO);
-                    const uint64_t db = LOW ? smem_desc(xa, LBO, SBO) : smem_desc(wa, LBO, SBO);
-                    const uint32_t acc = (s == 2) || kk != 0;
-                    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-                                 ::"r"(tb + (s ? 128u : 0u)), "l"(da), "l"(db), "r"(idesc), "r"(acc) : "memory");
+                for (int s = 0; s < 3; ++s) {
+#pragma unroll 1
+                    for (int kk = 0; kk < K / 16; ++kk) {
+                        // column block blk: operand rows [128 blk, 128 blk + 128)
+                        const uint32_t xa = su32(xs + s * SLICE) + (uint32_t)blk * 16u * SBO + kk * 2 * LBO;
+                        const uint32_t wa = su32(ws) + kk * 2 * LBO;
+                        const uint64_t da = LOW ? smem_desc(wa, LBO, SBO) : smem_desc(xa, LBO, SBO);
+                        const uint64_t db = LOW ? smem_desc(xa, LBO, SBO) : smem_desc(wa, LBO, SBO);
+                        const uint32_t acc = (s == 2) || kk != 0;
+                        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                                     ::"r"(tb + (uint32_t)(blk * 2 * N_MMA) + (s ? (uint32_t)N_MMA : 0u)), "l"(da),
+                                       "l"(db), "r"(idesc), "r"(acc) : "memory");
+                    }
                 }
             }
             // test hook: without the commit nothing arrives on mma_bar
@@ -447,7 +475,8 @@ cudaError_t encode_upper_map(CUtensorMap *m, void *amps, int n, int lo, int kb) 
     const cuuint64_t inner = 1ull << (lo + 1);
     const cuuint64_t dims[3] = {inner, 1ull << kb, 1ull << (n - lo - kb)};
     const cuuint64_t strides[2] = {inner * 4, (inner << kb) * 4};
-    const cuuint32_t box[3] = {(cuuint32_t)kCols, (cuuint32_t)(1u << kb), 1u};
+    const int cols = kCols * (128 >> kb);
+    const cuuint32_t box[3] = {(cuuint32_t)(cols < 256 ? cols : 256), (cuuint32_t)(1u << kb), 1u};
     const cuuint32_t estr[3] = {1u, 1u, 1u};
     const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, amps, dims, strides, box, estr,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -475,7 +504,8 @@ cudaError_t launch_tc_t(void *amps, int n, int lo, float scale, bool negate, int
                         int stall, cudaStream_t st, const Geometry &g) {
     constexpr int K = 1 << KB;
     // fp32 stage, three bf16 slices (128 rows), W (K rows), padded layout
-    const size_t smem = (size_t)K * (kCols / 2) * 8 + 3 * (size_t)(kCols / 8) * sbo_of(K) + (size_t)(K / 8) * sbo_of(K);
+    constexpr int COLS = tile_cols<KB, LOW>();
+    const size_t smem = (size_t)K * COLS * 4 + 3 * (size_t)(COLS / 8) * sbo_of(K) + (size_t)(K / 8) * sbo_of(K);
     auto kern = k_wht_tc<KB, LOW>;
     static bool attr = false;
     if (!attr) {
@@ -490,7 +520,7 @@ cudaError_t launch_tc_t(void *amps, int n, int lo, float scale, bool negate, int
         if (e != cudaSuccess) return e;
     }
     const uint64_t N = 1ull << n;
-    const uint64_t ntiles = N / ((uint64_t)(kCols / 2) * K);
+    const uint64_t ntiles = N / ((uint64_t)(COLS / 2) * K);
     const uint64_t grid = ntiles < (uint64_t)g.sm_count ? ntiles : (uint64_t)g.sm_count;
     kern<<<(unsigned)grid, kTcThreads, smem, st>>>(static_cast<float *>(amps), tmap, lo, ntiles, scale,
                                                    negate ? 1 : 0, status, wait_limit, stall);
@@ -501,7 +531,8 @@ cudaError_t launch_tc_t(void *amps, int n, int lo, float scale, bool negate, int
 
 bool tc_pass_supported(int n, int lo, int kb) {
     if (lo == 0) return kb == 7 && n >= 13;          // 64 blocks of 128 amplitudes per tile
-    return kb >= 5 && kb <= 7 && lo >= 6;            // 64 consecutive amplitudes below lo
+    // 64 * 128 / K consecutive amplitudes below lo
+    return kb >= 5 && kb <= 7 && lo >= 13 - kb && lo + kb <= n;
 }
 
 cudaError_t launch_wht_tc_pass(void *amps, int n, int lo, int kb, bool scaled, bool negate, int *status,
