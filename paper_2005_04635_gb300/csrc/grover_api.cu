@@ -11,6 +11,9 @@
 #include <string.h>
 
 #include <atomic>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "grover_internal.cuh"
 
@@ -115,6 +118,19 @@ grover_status ensure_mean(grover_state *s, const MarkedDev &mk, uint64_t key) {
 }  // namespace
 
 void grv::set_thread_error(const char *msg) { snprintf(g_err, sizeof g_err, "%s", msg); }
+
+cudaError_t grv::raise_func_attr(const void *kern, cudaFuncAttribute attr, int value) {
+    static std::mutex mu;
+    static std::map<std::tuple<const void *, int, int>, int> done;  // (kernel, device, attribute) -> value set
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    int &cur = done[std::make_tuple(kern, dev, (int)attr)];
+    if (cur >= value && cur != 0) return cudaSuccess;
+    if ((e = cudaFuncSetAttribute(kern, attr, value)) == cudaSuccess) cur = value;
+    return e;
+}
 
 extern "C" {
 

@@ -268,6 +268,16 @@ cudaError_t launch_phase_grid(const PhaseGridArgs &a, bool backward, unsigned G,
 // Sets the message grover_last_error(NULL) returns on this host thread.
 void set_thread_error(const char *msg);
 
+// ---- kernel attributes (grover_api.cu) ----------------------------------------
+// Raises a kernel attribute (a shared-memory limit, the non-portable cluster
+// permission) on the current device to at least `value`, once per device:
+// attributes belong to a device's context, so a process driving several GPUs
+// sets them on each.  Thread-safe.
+cudaError_t raise_func_attr(const void *kern, cudaFuncAttribute attr, int value);
+template <class F> cudaError_t raise_smem_limit(F kern, size_t smem) {
+    return raise_func_attr(reinterpret_cast<const void *>(kern), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
 }  // namespace grv
 
 // Handle layout (opaque in the C ABI).

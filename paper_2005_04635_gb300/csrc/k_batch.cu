@@ -199,7 +199,7 @@ k_batch(float4 *amps, const BatchInst *inst, const uint32_t *order, uint32_t cou
 template <int THREADS> cudaError_t prepare_t(const BatchLaunch &L, int sm_count, unsigned *grid) {
     auto kern = k_batch<THREADS>;
     const size_t smem = (size_t)L.onchip_vecs * sizeof(float4);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_smem_limit(kern, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, smem);

@@ -118,11 +118,9 @@ cudaError_t launch_wht_t(void *amps, int n, int lo, T scale, bool negate, cudaSt
     constexpr int MIDS = 1 << KB;
     const size_t smem = (size_t)MIDS * (kCols + kPad) * sizeof(C2<T>);
     auto kern = k_wht<T, KB, LOW>;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    {
+        cudaError_t e = raise_smem_limit(kern, smem);
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     const uint64_t N = 1ull << n;
     int cols = kCols;

@@ -507,11 +507,9 @@ cudaError_t launch_tc_t(void *amps, int n, int lo, float scale, bool negate, int
     constexpr int COLS = tile_cols<KB, LOW>();
     const size_t smem = (size_t)K * COLS * 4 + 3 * (size_t)(COLS / 8) * sbo_of(K) + (size_t)(K / 8) * sbo_of(K);
     auto kern = k_wht_tc<KB, LOW>;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    {
+        cudaError_t e = raise_smem_limit(kern, smem);
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     CUtensorMap tmap;
     memset(&tmap, 0, sizeof tmap);

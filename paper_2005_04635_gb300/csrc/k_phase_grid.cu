@@ -454,14 +454,9 @@ __global__ void __launch_bounds__(kPgThreads, 1) k_phase_grid_bwd(PhaseGridArgs 
     }
 }
 
-template <class F> cudaError_t launch_coop(F kern, unsigned G, size_t smem, cudaStream_t st, const PhaseGridArgs &a,
-                                           size_t *smem_set) {
+template <class F> cudaError_t launch_coop(F kern, unsigned G, size_t smem, cudaStream_t st, const PhaseGridArgs &a) {
     cudaError_t e;
-    if (smem > *smem_set) {
-        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-            return e;
-        *smem_set = smem;
-    }
+    if ((e = raise_smem_limit(kern, smem)) != cudaSuccess) return e;
     int per_sm = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPgThreads, smem)) != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorNotSupported;
@@ -506,9 +501,8 @@ cudaError_t launch_phase_table(const double *phi, const double *vphi, long long 
 }
 
 cudaError_t launch_phase_grid(const PhaseGridArgs &a, bool backward, unsigned G, size_t smem, cudaStream_t st) {
-    static size_t set_f = 0, set_b = 0;
-    if (backward) return launch_coop(k_phase_grid_bwd, G, smem, st, a, &set_b);
-    return launch_coop(k_phase_grid_fwd, G, smem, st, a, &set_f);
+    if (backward) return launch_coop(k_phase_grid_bwd, G, smem, st, a);
+    return launch_coop(k_phase_grid_fwd, G, smem, st, a);
 }
 
 }  // namespace grv

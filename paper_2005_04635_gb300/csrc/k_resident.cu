@@ -494,13 +494,8 @@ __global__ void __launch_bounds__(kRgThreads, 1) k_resident_grid(ResGridArgs a) 
 
 template <class T> cudaError_t launch_grid_t(const ResGridArgs &a, unsigned G, size_t smem, cudaStream_t st) {
     auto kern = k_resident_grid<T>;
-    static size_t smem_set = 0;
     cudaError_t e;
-    if (smem > smem_set) {
-        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-            return e;
-        smem_set = smem;
-    }
+    if ((e = raise_smem_limit(kern, smem)) != cudaSuccess) return e;
     int per_sm = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRgThreads, smem)) != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorNotSupported;
@@ -519,18 +514,11 @@ template <class T> cudaError_t launch_grid_t(const ResGridArgs &a, unsigned G, s
 
 template <class T> cudaError_t launch_cluster_t(const ResArgs &a, unsigned C, size_t smem, cudaStream_t st) {
     auto kern = k_resident_cluster<T>;
-    static size_t smem_set = 0;
     cudaError_t e;
-    if (smem > smem_set) {
-        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-            return e;
-        smem_set = smem;
-    }
-    static bool nonportable = false;
-    if (C > 8 && !nonportable) {
-        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess) return e;
-        nonportable = true;
-    }
+    if ((e = raise_smem_limit(kern, smem)) != cudaSuccess) return e;
+    if (C > 8 && (e = raise_func_attr(reinterpret_cast<const void *>(kern), cudaFuncAttributeNonPortableClusterSizeAllowed,
+                                      1)) != cudaSuccess)
+        return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C);
     cfg.blockDim = dim3(kResThreads);
