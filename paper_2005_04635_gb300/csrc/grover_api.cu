@@ -16,6 +16,7 @@
 #include <tuple>
 
 #include "grover_internal.cuh"
+#include "trace.cuh"
 
 using namespace grv;
 
@@ -272,6 +273,7 @@ grover_status grover_set_option(grover_state *s, grover_option opt, int64_t valu
 }
 
 grover_status grover_init_uniform(grover_state *s) {
+    GROVER_TRACE("grover_init_uniform");
     if (grover_status st = check_state(s)) return st;
     CK(s, launch_init_uniform(s->amps, s->n, s->dtype, s->stream, s->geo), "init launch");
     s->mu_valid = false;
@@ -279,6 +281,7 @@ grover_status grover_init_uniform(grover_state *s) {
 }
 
 grover_status grover_init_state(grover_state *s, const void *amps, int amps_on_device) {
+    GROVER_TRACE("grover_init_state");
     if (grover_status st = check_state(s)) return st;
     if (!amps) return fail(s, GROVER_EINVAL, "source amplitudes are NULL");
     const size_t bytes = s->N * amp_bytes(s->dtype);
@@ -403,6 +406,7 @@ grover_status grover_marked_destroy(grover_marked *mk) {
 }
 
 grover_status grover_oracle(grover_state *s, const grover_marked *mk) {
+    GROVER_TRACE("grover_oracle");
     if (grover_status st = check_state(s)) return st;
     if (grover_status st = check_marked(s, mk)) return st;
     if (mk->dev.m == 0) return GROVER_OK;
@@ -414,6 +418,7 @@ grover_status grover_oracle(grover_state *s, const grover_marked *mk) {
 }
 
 grover_status grover_diffuse(grover_state *s) {
+    GROVER_TRACE("grover_diffuse");
     if (grover_status st = check_state(s)) return st;
     const MarkedDev none = no_marks();
     if (grover_status st = ensure_mean(s, none, 0)) return st;
@@ -426,6 +431,7 @@ grover_status grover_diffuse(grover_state *s) {
 }
 
 grover_status grover_iterate(grover_state *s, const grover_marked *mk, uint64_t k) {
+    GROVER_TRACE("grover_iterate");
     if (grover_status st = check_state(s)) return st;
     if (grover_status st = check_marked(s, mk)) return st;
     if (k == 0) return GROVER_OK;
@@ -510,6 +516,7 @@ grover_status grover_iterate(grover_state *s, const grover_marked *mk, uint64_t 
 }
 
 grover_status grover_iterate_gate(grover_state *s, const grover_marked *mk, uint64_t k) {
+    GROVER_TRACE("grover_iterate_gate");
     if (grover_status st = check_state(s)) return st;
     if (grover_status st = check_marked(s, mk)) return st;
     if (k == 0) return GROVER_OK;
@@ -546,6 +553,7 @@ grover_status grover_iterate_gate(grover_state *s, const grover_marked *mk, uint
 
 grover_status grover_iterate_circuit(grover_state *s, const grover_marked *mk, uint64_t k, uint64_t *gates_out,
                                      uint64_t *passes_out) {
+    GROVER_TRACE("grover_iterate_circuit");
     if (grover_status st = check_state(s)) return st;
     if (grover_status st = check_marked(s, mk)) return st;
     if (mk->dev.m > 0 && !mk->host_list)
@@ -602,6 +610,7 @@ grover_status grover_iterate_circuit(grover_state *s, const grover_marked *mk, u
 }
 
 grover_status grover_measure_probs(grover_state *s, double *out, int out_on_device) {
+    GROVER_TRACE("grover_measure_probs");
     if (grover_status st = check_state(s)) return st;
     if (!out) return fail(s, GROVER_EINVAL, "output is NULL");
     if (out_on_device) {
@@ -620,6 +629,7 @@ grover_status grover_measure_probs(grover_state *s, double *out, int out_on_devi
 }
 
 grover_status grover_measure_topm(grover_state *s, size_t m, uint64_t *idx, double *p) {
+    GROVER_TRACE("grover_measure_topm");
     if (grover_status st = check_state(s)) return st;
     if (!idx || !p) return fail(s, GROVER_EINVAL, "output is NULL");
     if (m < 1 || m > (size_t)kTopMMax || m > s->N)
@@ -638,6 +648,7 @@ grover_status grover_measure_topm(grover_state *s, size_t m, uint64_t *idx, doub
 }
 
 grover_status grover_success_prob(grover_state *s, const grover_marked *mk, double *p_success, double *norm) {
+    GROVER_TRACE("grover_success_prob");
     if (grover_status st = check_state(s)) return st;
     if (grover_status st = check_marked(s, mk)) return st;
     CK(s, launch_norm_success(s->amps, s->n, s->dtype, mk->dev, s->sc, s->stream, s->geo), "norm launch");

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "grover_internal.cuh"
+#include "trace.cuh"
 
 using namespace grv;
 
@@ -178,6 +179,7 @@ grover_status grover_batch_create(grover_batch **out, size_t count, const int *n
 }
 
 grover_status grover_batch_run(grover_batch *b) {
+    GROVER_TRACE("grover_batch_run");
     if (!b) return bfail(nullptr, GROVER_EINVAL, "batch is NULL");
     cudaError_t e = cudaGraphLaunch(b->exec, b->stream);
     if (e != cudaSuccess) return bfail(b, GROVER_ECUDA, "batch graph launch", e);
@@ -185,6 +187,7 @@ grover_status grover_batch_run(grover_batch *b) {
 }
 
 grover_status grover_batch_tune(grover_batch *b, int *threads_out, uint32_t *onchip_vecs_out) {
+    GROVER_TRACE("grover_batch_tune");
     if (!b) return bfail(nullptr, GROVER_EINVAL, "batch is NULL");
     static const int kThreadsOpts[] = {256, 512, 1024};
     static const uint32_t kOnchipOpts[] = {2048, 4096, 8192};  // 32, 64, 128 KiB

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include "grover_internal.cuh"
+#include "trace.cuh"
 
 using namespace grv;
 
@@ -150,6 +151,7 @@ extern "C" {
 
 grover_status grover_phase_forward(grover_state *s, const grover_marked *mk, const double *phi, const double *vphi,
                                    uint64_t K, double *stats) {
+    GROVER_TRACE("grover_phase_forward");
     if (grover_status st = check_common(s, mk, phi, vphi, K)) return st;
     if (stats && !on_device(stats, s->geo.dev))
         return pfail(s, GROVER_EINVAL, "stats must be device memory of the state's device");
@@ -180,6 +182,7 @@ grover_status grover_phase_forward(grover_state *s, const grover_marked *mk, con
 
 grover_status grover_phase_backward(grover_state *s, const grover_marked *mk, const double *phi, const double *vphi,
                                     uint64_t K, void *lam, double *grad_phi, double *grad_vphi) {
+    GROVER_TRACE("grover_phase_backward");
     if (grover_status st = check_common(s, mk, phi, vphi, K)) return st;
     if (!lam || (uintptr_t)lam % 16 != 0 || !on_device(lam, s->geo.dev))
         return pfail(s, GROVER_EINVAL, "lambda must be 16-byte aligned device memory of the state's device");

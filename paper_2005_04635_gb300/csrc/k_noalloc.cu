@@ -22,6 +22,7 @@
 #include <mutex>
 
 #include "grover_internal.cuh"
+#include "trace.cuh"
 
 namespace {
 
@@ -78,6 +79,7 @@ bool is_device_pointer(const void *p, int dev) {
 extern "C" grover_status grover_iterate_noalloc(void *dev_amps, int n, grover_dtype dtype,
                                                 const uint64_t *dev_marked, size_t m, uint64_t k,
                                                 void *cuda_stream) {
+    GROVER_TRACE("grover_iterate_noalloc");
     using namespace grv;
     if (dtype != GROVER_C64 && dtype != GROVER_C128) return noalloc_fail(GROVER_EINVAL, "unknown dtype");
     const int nmax = dtype == GROVER_C64 ? 33 : 32;
