@@ -154,7 +154,7 @@ def test_forward_k0_is_loss_of_start(B, path):
 
 @pytest.mark.parametrize("path", ["auto", "pass"])
 def test_uniform_n20_matches_reduced_model(B, path):
-    """Config: n = 20, M = 3, K = 32, phases U(0, 2 pi): loss and the two
+    """Workload n = 20, M = 3, K = 32, phases U(0, 2 pi): loss and the two
     amplitudes against the exact FP64 reduced model."""
     n, m, K = 20, 3, 32
     marked = inputs.marked_indices(n, m, seed=750)
@@ -211,7 +211,7 @@ def test_gradients_match_oracle_fd(B, n, m, K, path):
 
 
 @pytest.mark.parametrize("path", ["auto", "pass"])
-def test_config_n20_gradients(B, path):
+def test_n20_gradients(B, path):
     """n = 20, M = 3, K = 32, uniform start: adjoint gradients against the FP64
     reduced model (central differences, h = 1e-6) and against central
     differences of the GPU loss (h = 1e-4)."""
@@ -321,7 +321,7 @@ def test_rejects_unsupported(B):
 
 # ---- autograd and training -------------------------------------------------------------
 def test_autograd_function_and_adam(B):
-    """Config: n = 20, M = 3, K = 32, phases U(0, 2 pi), 200 Adam steps."""
+    """Workload n = 20, M = 3, K = 32, phases U(0, 2 pi), 200 Adam steps."""
     from paper_2005_04635_gb300.autograd import phase_search_loss
     n, m, K = 20, 3, 32
     marked = inputs.marked_indices(n, m, seed=750)
