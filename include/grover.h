@@ -289,9 +289,22 @@ grover_status grover_batch_create(grover_batch **out, size_t count, const int *n
 grover_status grover_batch_run(grover_batch *b);
 
 /* Times the batch under each thread count (256, 512, 1024) and on-chip
- * threshold (32, 64, 128 KiB) and keeps the fastest (the batch runs 18 times);
- * the choice is returned if the pointers are not NULL.  Synchronous. */
+ * threshold (32, 64, 128 KiB) of the one-CTA kernel and keeps the fastest,
+ * then times the whole batch with one CTA per instance against clusters of 16
+ * for the large instances (grover_batch_set_packing) and keeps the faster
+ * (the batch runs about 22 times); the kernel choice is returned if the
+ * pointers are not NULL.  Synchronous. */
 grover_status grover_batch_tune(grover_batch *b, int *threads, uint32_t *onchip_vecs);
+
+/* How instances map to the GPU: 0 or 1 (the default) runs every instance on
+ * one CTA; 16 runs each instance with n >= 17 on one thread-block cluster of
+ * 16 CTAs -- each CTA a slice of the state, in shared memory up to
+ * 200 KiB per CTA (n <= 18), else streamed through L2 with one large state per
+ * cluster live; the exact partial sums of an iteration meet through
+ * distributed shared memory after a hardware cluster barrier -- and the rest
+ * one per CTA.  GROVER_EINVAL for other values, GROVER_EUNSUPPORTED for 16
+ * where clusters cannot run.  Rebuilds the captured graph. */
+grover_status grover_batch_set_packing(grover_batch *b, int cluster_size);
 
 /* Copies the count success probabilities sum_marked |c_x|^2 (FP64) of the last
  * run to the HOST array p_success.  Synchronous. */

@@ -51,6 +51,7 @@ _SIGS = {
     "grover_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_size_t, _vp, _vp, _vp, _vp, _vp, ctypes.c_uint64, _vp]),
     "grover_batch_run": (ctypes.c_int, [_vp]),
     "grover_batch_tune": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_uint32)]),
+    "grover_batch_set_packing": (ctypes.c_int, [_vp, ctypes.c_int]),
     "grover_batch_success": (ctypes.c_int, [_vp, _vp]),
     "grover_batch_destroy": (ctypes.c_int, [_vp]),
     "grover_phase_forward": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_uint64, _vp]),
@@ -299,6 +300,10 @@ class Batch:
         th, oc = ctypes.c_int(), ctypes.c_uint32()
         _check(lib().grover_batch_tune(self.handle, ctypes.byref(th), ctypes.byref(oc)))
         return th.value, oc.value
+
+    def set_packing(self, cluster_size: int):
+        """16: clusters of 16 CTAs for instances with n >= 17; 0 or 1: one CTA each."""
+        _check(lib().grover_batch_set_packing(self.handle, int(cluster_size)))
 
     def success(self):
         p = np.empty(self.count, dtype=np.float64)

@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <new>
 #include <numeric>
 #include <vector>
 
@@ -21,9 +22,15 @@ struct grover_batch {
     cudaStream_t stream;
     int sm_count;
     float4 *amps;
-    void *dev_mem;          // instance table, order, marked lists, counter, results
-    BatchLaunch L;
+    void *dev_mem;          // instance table, orders, marked lists, counters, results
+    BatchLaunch L;          // small instances, one CTA each
+    BatchClusterLaunch LC;  // large instances, one cluster each
     unsigned grid;
+    int clusters;           // co-resident clusters (0: cluster packing unavailable)
+    int packing;            // 0: one CTA per instance; kBatchClusterSize: clusters for large instances
+    uint32_t *order_dev;    // [2 * count]: small order, then large order
+    std::vector<uint32_t> order;  // all instances, largest N * k first
+    std::vector<int> nq;    // qubits per instance
     cudaGraph_t graph;
     cudaGraphExec_t exec;
     bool graph_ready;
@@ -47,6 +54,25 @@ grover_status bfail(grover_batch *b, grover_status st, const char *msg, cudaErro
     return st;
 }
 
+// Splits the instances between the two kernels (large ones to clusters when
+// packing is on and clusters can run) and uploads both orders.
+grover_status split(grover_batch *b) {
+    const bool use = b->packing > 1 && b->clusters > 0;
+    std::vector<uint32_t> small, large;
+    for (uint32_t i : b->order) ((use && b->nq[i] >= kBatchClusterMinQubits) ? large : small).push_back(i);
+    cudaError_t e = cudaSuccess;
+    if (!small.empty())
+        e = cudaMemcpy(b->order_dev, small.data(), small.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !large.empty())
+        e = cudaMemcpy(b->order_dev + b->count, large.data(), large.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bfail(b, GROVER_ECUDA, "upload of the batch orders", e);
+    b->L.order = b->order_dev;
+    b->L.count = (uint32_t)small.size();
+    b->LC.order = b->order_dev + b->count;
+    b->LC.count = (uint32_t)large.size();
+    return GROVER_OK;
+}
+
 grover_status rebuild(grover_batch *b) {
     if (b->graph_ready) {
         cudaGraphExecDestroy(b->exec);
@@ -55,12 +81,15 @@ grover_status rebuild(grover_batch *b) {
     }
     cudaError_t e = prepare_batch(b->L, b->sm_count, &b->grid);
     if (e != cudaSuccess) return bfail(b, GROVER_ECUDA, "batch kernel set-up", e);
+    if (grover_status st = split(b)) return st;
     cudaStream_t cs;
     if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess)
         return bfail(b, GROVER_ECUDA, "capture stream", e);
     e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        cudaError_t e2 = enqueue_batch(b->L, b->grid, cs);
+        // large instances first (they hold the longest runs), then the small ones
+        cudaError_t e2 = b->LC.count ? enqueue_batch_cluster(b->LC, b->clusters, cs) : cudaSuccess;
+        if (e2 == cudaSuccess) e2 = enqueue_batch(b->L, b->grid, cs);
         e = cudaStreamEndCapture(cs, &b->graph);
         if (e2 != cudaSuccess) e = e2;
     }
@@ -126,8 +155,11 @@ grover_status grover_batch_create(grover_batch **out, size_t count, const int *n
         return (double)(1ull << inst[a].n) * (double)(inst[a].k + 1) > (double)(1ull << inst[b].n) * (double)(inst[b].k + 1);
     });
 
-    grover_batch *b = (grover_batch *)calloc(1, sizeof(grover_batch));
+    grover_batch *b = new (std::nothrow) grover_batch();
     if (!b) return bfail(nullptr, GROVER_ENOMEM, "host allocation of the batch");
+    b->order = order;
+    b->nq.resize(count);
+    for (size_t i = 0; i < count; ++i) b->nq[i] = inst[i].n;
     b->count = count;
     b->stream = (cudaStream_t)cuda_stream;
     b->amps = (float4 *)dev_amps;
@@ -136,16 +168,16 @@ grover_status grover_batch_create(grover_batch **out, size_t count, const int *n
     cudaError_t e;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
         (e = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) {
-        free(b);
+        delete b;
         return bfail(nullptr, GROVER_ECUDA, "device query", e);
     }
     const size_t s_inst = ((count * sizeof(BatchInst)) + 255) & ~size_t(255);
-    const size_t s_order = ((count * sizeof(uint32_t)) + 255) & ~size_t(255);
+    const size_t s_order = ((2 * count * sizeof(uint32_t)) + 255) & ~size_t(255);
     const size_t s_mark = ((std::max<uint64_t>(total_marked, 1) * sizeof(uint64_t)) + 255) & ~size_t(255);
     const size_t s_next = 256, s_res = ((count * sizeof(double)) + 255) & ~size_t(255);
     char *mem = nullptr;
     if ((e = cudaMalloc((void **)&mem, s_inst + s_order + s_mark + s_next + s_res)) != cudaSuccess) {
-        free(b);
+        delete b;
         return bfail(nullptr, GROVER_ENOMEM, "device allocation of the batch tables", e);
     }
     b->dev_mem = mem;
@@ -159,19 +191,29 @@ grover_status grover_batch_create(grover_batch **out, size_t count, const int *n
     L.count = (uint32_t)count;
     L.onchip_vecs = 8192;  // 128 KiB: instances up to n = 14
     L.threads = 512;
+    b->order_dev = (uint32_t *)(mem + s_inst);
+    BatchClusterLaunch &LC = b->LC;
+    LC.amps = b->amps;
+    LC.inst = L.inst;
+    LC.marked = L.marked;
+    LC.next = L.next + 32;  // its own counter, 128 bytes after the first
+    LC.psucc = L.psucc;
+    if (prepare_batch_cluster(&b->clusters) != cudaSuccess) {
+        (void)cudaGetLastError();
+        b->clusters = 0;
+    }
+    b->packing = 0;  // one CTA per instance; grover_batch_tune also tries clusters
     if ((e = cudaMemcpy((void *)L.inst, inst.data(), count * sizeof(BatchInst), cudaMemcpyHostToDevice)) !=
-            cudaSuccess ||
-        (e = cudaMemcpy((void *)L.order, order.data(), count * sizeof(uint32_t), cudaMemcpyHostToDevice)) !=
             cudaSuccess ||
         (total_marked && (e = cudaMemcpy((void *)L.marked, marked, total_marked * sizeof(uint64_t),
                                          cudaMemcpyHostToDevice)) != cudaSuccess)) {
         cudaFree(mem);
-        free(b);
+        delete b;
         return bfail(nullptr, GROVER_ECUDA, "upload of the batch tables", e);
     }
     if (grover_status st = rebuild(b)) {
         cudaFree(mem);
-        free(b);
+        delete b;
         return st;
     }
     *out = b;
@@ -195,6 +237,9 @@ grover_status grover_batch_tune(grover_batch *b, int *threads_out, uint32_t *onc
     cudaError_t e;
     if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess)
         return bfail(b, GROVER_ECUDA, "tuner events", e);
+    // the one-CTA kernel's shape is tuned over every instance
+    b->packing = 0;
+    if (grover_status st = split(b)) return st;
     BatchLaunch best = b->L;
     float best_ms = 3.4e38f;
     for (int th : kThreadsOpts) {
@@ -222,14 +267,51 @@ grover_status grover_batch_tune(grover_batch *b, int *threads_out, uint32_t *onc
             }
         }
     }
+    if (best_ms > 3.3e38f) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return bfail(b, GROVER_ECUDA, "no batch configuration could run");
+    }
+    b->L = best;
+    // then whole graphs: one CTA per instance against clusters for the large ones
+    b->packing = 0;
+    if (grover_status st = rebuild(b)) return st;
+    if (b->clusters > 0) {
+        auto time_graph = [&](float *ms) {
+            return cudaGraphLaunch(b->exec, b->stream) == cudaSuccess && cudaEventRecord(e0, b->stream) == cudaSuccess &&
+                   cudaGraphLaunch(b->exec, b->stream) == cudaSuccess && cudaEventRecord(e1, b->stream) == cudaSuccess &&
+                   cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(ms, e0, e1) == cudaSuccess;
+        };
+        float t_one = 0.f, t_cluster = 0.f;
+        const bool ok1 = time_graph(&t_one);
+        b->packing = kBatchClusterSize;
+        grover_status st = rebuild(b);
+        const bool ok2 = st == GROVER_OK && time_graph(&t_cluster);
+        if (!ok1 || !ok2 || t_cluster >= t_one) {
+            (void)cudaGetLastError();
+            b->packing = 0;
+            if ((st = rebuild(b)) != GROVER_OK) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return st;
+            }
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (best_ms > 3.3e38f) return bfail(b, GROVER_ECUDA, "no batch configuration could run");
-    b->L = best;
-    if (grover_status st = rebuild(b)) return st;
     if (threads_out) *threads_out = best.threads;
     if (onchip_vecs_out) *onchip_vecs_out = best.onchip_vecs;
     return GROVER_OK;
+}
+
+grover_status grover_batch_set_packing(grover_batch *b, int cluster_size) {
+    if (!b) return bfail(nullptr, GROVER_EINVAL, "batch is NULL");
+    if (cluster_size != 0 && cluster_size != 1 && cluster_size != kBatchClusterSize)
+        return bfail(b, GROVER_EINVAL, "cluster size must be 0, 1 or 16");
+    if (cluster_size == kBatchClusterSize && b->clusters == 0)
+        return bfail(b, GROVER_EUNSUPPORTED, "clusters of 16 CTAs cannot run on this device");
+    b->packing = cluster_size;
+    return rebuild(b);
 }
 
 grover_status grover_batch_success(grover_batch *b, double *p_success) {
@@ -248,7 +330,7 @@ grover_status grover_batch_destroy(grover_batch *b) {
         cudaGraphDestroy(b->graph);
     }
     cudaFree(b->dev_mem);
-    free(b);
+    delete b;
     if (e != cudaSuccess) return bfail(nullptr, GROVER_ECUDA, "grover_batch_destroy", e);
     return GROVER_OK;
 }

@@ -198,6 +198,27 @@ cudaError_t prepare_batch(const BatchLaunch &L, int sm_count, unsigned *grid);
 // Resets the work counter and launches (capturable in a CUDA graph).
 cudaError_t enqueue_batch(const BatchLaunch &L, unsigned grid, cudaStream_t st);
 
+// Large instances run one per thread-block cluster of kBatchClusterSize CTAs
+// (each CTA a slice of the state; exact partials combined through distributed
+// shared memory after a hardware cluster barrier per iteration), the small
+// ones one per CTA (k_batch).
+constexpr int kBatchClusterSize = 16;
+constexpr int kBatchClusterMinQubits = 17;     // smallest n run by a cluster
+constexpr uint32_t kBatchClusterOnchipVecs = 12800;  // slice kept in shared memory up to 200 KiB
+struct BatchClusterLaunch {
+    float4 *amps;
+    const BatchInst *inst;
+    const uint32_t *order;  // the large instances, largest N * k first
+    uint32_t count;
+    const uint64_t *marked;
+    unsigned *next;         // work counter
+    double *psucc;
+};
+// Sets the attributes and returns the number of co-resident clusters (0 if
+// clusters of kBatchClusterSize cannot run).
+cudaError_t prepare_batch_cluster(int *clusters);
+cudaError_t enqueue_batch_cluster(const BatchClusterLaunch &L, int clusters, cudaStream_t st);
+
 // ---- generalised phase iterator and its adjoint (k_phase.cu), complex64 ----
 constexpr int kPhaseMaxGrid = 2048;  // CTAs of a phase-iterator launch
 constexpr uint64_t kPhaseMaxMarked = 256;

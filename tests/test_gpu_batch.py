@@ -91,3 +91,31 @@ def test_batch_rejects_bad_input(B):
         B.Batch([27], [3], [[1]])  # n too large
     with pytest.raises(B.GroverError):
         B.Batch([10], [3], [list(range(65))])  # more than 64 marked
+
+
+@pytest.mark.parametrize("packing", [16, 0])
+def test_batch_large_instances_both_packings(B, packing):
+    """Instances with n = 15..20 (clusters of 16 CTAs for n >= 17: on chip up to
+    n = 18, streamed through L2 above), mixed with small ones, against the
+    closed form under both packings."""
+    ns, ks, marks = make_instances(40, 15, 20, 8, seed=31)
+    ns2, ks2, marks2 = make_instances(40, 3, 12, 8, seed=32)
+    b = B.Batch(ns + ns2, ks + ks2, marks + marks2)
+    b.set_packing(packing)
+    b.run()
+    p = b.success()
+    torch.cuda.synchronize()
+    all_n, all_k, all_m = ns + ns2, ks + ks2, marks + marks2
+    for i in range(len(all_n)):
+        got = b.state(i).cpu().numpy()
+        pref = check_instance(got, all_n[i], all_m[i], all_k[i])
+        assert abs(p[i] - pref) <= 1e-4
+    b.run()
+    assert np.array_equal(b.success(), p)  # deterministic
+
+
+def test_batch_packing_rejects_bad_size(B):
+    b = B.Batch([5], [2], [[3]])
+    with pytest.raises(B.GroverError) as ei:
+        b.set_packing(8)
+    assert ei.value.status == 1
