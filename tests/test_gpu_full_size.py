@@ -82,3 +82,38 @@ def test_n33_c64_100_iterations(B):
     if free < (80 << 30):
         pytest.skip("needs 80 GB of free device memory")
     run_and_check(B, 33, 1, "c64", 100, seed=3300)
+
+
+def test_n32_c128_maximum_size(B):
+    """The largest complex128 state the ABI accepts (2^32 amplitudes, 64 GiB)."""
+    free, _ = torch.cuda.mem_get_info()
+    if free < (80 << 30):
+        pytest.skip("needs 80 GB of free device memory")
+    run_and_check(B, 32, 4, "c128", 20, seed=3204)
+
+
+def test_n33_c64_bitmask_marked_set(B):
+    """n = 33 with M = 300 marked indices: above the list limit, so the oracle
+    flip reads the 1 GiB bitmask in the same fused pass."""
+    free, _ = torch.cuda.mem_get_info()
+    if free < (80 << 30):
+        pytest.skip("needs 80 GB of free device memory")
+    n, m, k = 33, 300, 12
+    marked = inputs.marked_indices(n, m, seed=3330)
+    mk = B.Marked(n, marked)
+    st = B.State(n, "c64")
+    st.init_uniform()
+    st.iterate(mk, k)
+    ps, _ = st.success_prob(mk)
+    st.sync()
+    a = st.amps
+    mvals = a[torch.as_tensor(marked.astype(np.int64), device=a.device)]
+    assert bool(torch.all(mvals == mvals[0]).item())
+    am, au = oracle.closed_form_uniform(n, m, k)
+    tol = 3 * k * 2.0 ** -24
+    assert abs(complex(mvals[0].item()) - am) <= tol
+    u = next(x for x in range(m + 1) if x not in set(marked.tolist()))
+    assert abs(complex(a[u].item()) - au) <= tol
+    assert abs(ps - m * am * am) <= 1e-4
+    del st
+    torch.cuda.empty_cache()
