@@ -77,6 +77,25 @@ __device__ __forceinline__ uint32_t kmaj_off(int row, int k, int K) {
     return (uint32_t)((row >> 3) * sbo_of(K) + (k >> 3) * kLBO + (row & 7) * 16 + (k & 7) * 2);
 }
 
+// 128-byte-swizzle K-major operand layout (groups of 6 and 7 bits, K >= 64):
+// a row's 64 elements of one K chunk fill 128 bytes, 8 rows form a 1024-byte
+// atom, and the 16-byte chunk c of row r sits at chunk c ^ (r % 8); the K
+// chunks of an R-row operand follow one another, R / 8 atoms each.  The
+// tensor cores read it at full shared-memory width (the padded layout's
+// 144-byte core-matrix stride straddles 128-byte lines), and stores whose 8
+// rows differ in r % 8, or whose 8 chunks differ, are conflict-free.
+__device__ __forceinline__ uint32_t sw_off(int row, int k, int R) {
+    const int kc = k >> 6, kin = k & 63;
+    return (uint32_t)(kc * (R >> 3) * 1024 + (row >> 3) * 1024 + (row & 7) * 128) +
+           ((uint32_t)((kin >> 3) ^ (row & 7)) << 4) + (uint32_t)(kin & 7) * 2;
+}
+// descriptor of that layout: SBO 1024 B between 8-row atoms, LBO unused (16),
+// layout field 2 (128-byte swizzle); atoms start on 1024-byte boundaries
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
 __device__ __forceinline__ void split3(float x, float &b0, float &b1, float &b2) {
     const __nv_bfloat16 h0 = __float2bfloat16_rn(x);
     float r = x - __bfloat162float(h0);
@@ -90,12 +109,12 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
     const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<const uint32_t *>(&p);
 }
-// stores 8 consecutive-k values of one column (row) into the three slices
-__device__ __forceinline__ void put8(unsigned char *xs, size_t slice_bytes, int row, int k0, int K, const float *v) {
+// stores 8 consecutive-k values of one column (row) into the three slices at
+// byte offset off (16-byte aligned) of each
+__device__ __forceinline__ void put8(unsigned char *xs, size_t slice_bytes, uint32_t off, const float *v) {
     float b[3][8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) split3(v[j], b[0][j], b[1][j], b[2][j]);
-    const uint32_t off = kmaj_off(row, k0, K);
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
         uint4 q;
@@ -198,10 +217,11 @@ k_wht_tc(float *amps, const __grid_constant__ CUtensorMap tmap, int lo, uint64_t
     constexpr int K = 1 << KB;
     constexpr int COLS = tile_cols<KB, LOW>();            // real columns (operand rows)
     constexpr int NB = COLS / kCols;                        // column blocks of 128 (MMA M)
+    constexpr bool SW = KB >= 6;                            // 128-byte-swizzle operands
     constexpr size_t STAGE = (size_t)K * COLS * 4;          // fp32 tile, 64 KiB
     constexpr uint32_t SBO = sbo_of(K);
     constexpr uint32_t LBO = kLBO;
-    constexpr size_t SLICE = (size_t)(COLS / 8) * SBO;      // one bf16 slice of the tile
+    constexpr size_t SLICE = SW ? (size_t)COLS * K * 2 : (size_t)(COLS / 8) * SBO;  // one bf16 slice of the tile
     constexpr int M_MMA = 128;
     constexpr int N_MMA = LOW ? kCols : K;                  // accumulator columns; A12 sits N_MMA after A0
     static_assert(!LOW || KB == 7, "the lowest group uses W as the 128-row operand");
@@ -231,7 +251,7 @@ k_wht_tc(float *amps, const __grid_constant__ CUtensorMap tmap, int lo, uint64_t
         q.y = pack2(v[2], v[3]);
         q.z = pack2(v[4], v[5]);
         q.w = pack2(v[6], v[7]);
-        *reinterpret_cast<uint4 *>(ws + kmaj_off(n, k0, K)) = q;
+        *reinterpret_cast<uint4 *>(ws + (SW ? sw_off(n, k0, K) : kmaj_off(n, k0, K))) = q;
     }
     if (tid == 0) {
         s_abort = 0;
@@ -361,13 +381,27 @@ k_wht_tc(float *amps, const __grid_constant__ CUtensorMap tmap, int lo, uint64_t
                     re[2 * q + 1] = c.z;
                     im[2 * q + 1] = c.w;
                 }
-                put8(xs, SLICE, 2 * o, kg * 8, K, re);
-                put8(xs, SLICE, 2 * o + 1, kg * 8, K, im);
+                put8(xs, SLICE, SW ? sw_off(2 * o, kg * 8, COLS) : kmaj_off(2 * o, kg * 8, K), re);
+                put8(xs, SLICE, SW ? sw_off(2 * o + 1, kg * 8, COLS) : kmaj_off(2 * o + 1, kg * 8, K), im);
             }
         } else {
-            // unit = (k-group of 8 mids, float4 column group); copy b of the
-            // tile holds columns [b BOX, (b + 1) BOX) as a [K][BOX] block
+            // copy b of the tile holds columns [b BOX, (b + 1) BOX) as a [K][BOX] block
             constexpr int BOX = box_cols<KB>();
+            if constexpr (SW) {
+                // unit = (k-group of 8 mids, column): consecutive threads read
+                // consecutive columns of each mid row and store rows whose r % 8
+                // differ (both conflict-free)
+                const float *stf = reinterpret_cast<const float *>(stage);
+                for (int u = tid; u < (K / 8) * COLS; u += kTcThreads) {
+                    const int c = u % COLS, kg = u / COLS;
+                    const float *src = stf + (size_t)(c / BOX) * K * BOX + (size_t)(kg * 8) * BOX + (c % BOX);
+                    float col[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) col[j] = src[(size_t)j * BOX];
+                    put8(xs, SLICE, sw_off(c, kg * 8, COLS), col);
+                }
+            } else
+            // unit = (k-group of 8 mids, float4 column group)
             for (int u = tid; u < (K / 8) * (COLS / 4); u += kTcThreads) {
                 const int c4 = u % (COLS / 4), kg = u / (COLS / 4);
                 const int bx = (4 * c4) / BOX, w4 = ((4 * c4) % BOX) / 4;
@@ -382,7 +416,7 @@ k_wht_tc(float *amps, const __grid_constant__ CUtensorMap tmap, int lo, uint64_t
                     col[3][j] = c.w;
                 }
 #pragma unroll
-                for (int q = 0; q < 4; ++q) put8(xs, SLICE, 4 * c4 + q, kg * 8, K, col[q]);
+                for (int q = 0; q < 4; ++q) put8(xs, SLICE, kmaj_off(4 * c4 + q, kg * 8, K), col[q]);
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -404,10 +438,18 @@ k_wht_tc(float *amps, const __grid_constant__ CUtensorMap tmap, int lo, uint64_t
 #pragma unroll 1
                     for (int kk = 0; kk < K / 16; ++kk) {
                         // column block blk: operand rows [128 blk, 128 blk + 128)
-                        const uint32_t xa = su32(xs + s * SLICE) + (uint32_t)blk * 16u * SBO + kk * 2 * LBO;
-                        const uint32_t wa = su32(ws) + kk * 2 * LBO;
-                        const uint64_t da = LOW ? smem_desc(wa, LBO, SBO) : smem_desc(xa, LBO, SBO);
-                        const uint64_t db = LOW ? smem_desc(xa, LBO, SBO) : smem_desc(wa, LBO, SBO);
+                        uint64_t dx, dw;
+                        if constexpr (SW) {
+                            const uint32_t kin = (uint32_t)(kk & 3) * 32u, kc = (uint32_t)(kk >> 2);
+                            dx = smem_desc_sw128(su32(xs + s * SLICE) + kc * (COLS / 8) * 1024u + (uint32_t)blk * 16u * 1024u +
+                                                 kin);
+                            dw = smem_desc_sw128(su32(ws) + kc * (K / 8) * 1024u + kin);
+                        } else {
+                            dx = smem_desc(su32(xs + s * SLICE) + (uint32_t)blk * 16u * SBO + kk * 2 * LBO, LBO, SBO);
+                            dw = smem_desc(su32(ws) + kk * 2 * LBO, LBO, SBO);
+                        }
+                        const uint64_t da = LOW ? dw : dx;
+                        const uint64_t db = LOW ? dx : dw;
                         const uint32_t acc = (s == 2) || kk != 0;
                         asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                                      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
@@ -505,7 +547,8 @@ cudaError_t launch_tc_t(void *amps, int n, int lo, float scale, bool negate, int
     constexpr int K = 1 << KB;
     // fp32 stage, three bf16 slices (128 rows), W (K rows), padded layout
     constexpr int COLS = tile_cols<KB, LOW>();
-    const size_t smem = (size_t)K * COLS * 4 + 3 * (size_t)(COLS / 8) * sbo_of(K) + (size_t)(K / 8) * sbo_of(K);
+    const size_t smem = KB >= 6 ? (size_t)K * COLS * 4 + 3 * (size_t)COLS * K * 2 + (size_t)K * K * 2
+                                : (size_t)K * COLS * 4 + 3 * (size_t)(COLS / 8) * sbo_of(K) + (size_t)(K / 8) * sbo_of(K);
     auto kern = k_wht_tc<KB, LOW>;
     {
         cudaError_t e = raise_smem_limit(kern, smem);
