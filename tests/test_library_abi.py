@@ -110,3 +110,18 @@ def test_null_handles(lib):
         assert getattr(lib, fn)(None) == 1
     assert lib.grover_iterate(None, None, 1) == 1
     assert lib.grover_destroy(None) == 0 and lib.grover_marked_destroy(None) == 0
+
+
+def test_null_handles_of_the_extended_calls(lib):
+    """Host-side validation of the phase, circuit, batch and allocation-free calls
+    (no device work is reached)."""
+    assert lib.grover_phase_forward(None, None, None, None, 0, None) == 1
+    assert lib.grover_phase_backward(None, None, None, None, 0, None, None, None) == 1
+    assert lib.grover_iterate_circuit(None, None, 1, None, None) == 1
+    assert lib.grover_iterate_gate(None, None, 1) == 1
+    assert lib.grover_batch_set_packing(None, 16) == 1
+    assert lib.grover_batch_run(None) == 1
+    assert lib.grover_batch_destroy(None) == 0
+    assert lib.grover_batch_amps_needed(2, (ctypes.c_int * 2)(5, 27)) == 0  # n above 26
+    assert lib.grover_batch_amps_needed(2, (ctypes.c_int * 2)(5, 6)) == 32 + 64
+    assert lib.grover_iterate_noalloc(None, 10, 0, None, 0, 1, None) == 1
