@@ -478,14 +478,12 @@ grover_status grover_iterate(grover_state *s, const grover_marked *mk, uint64_t 
             r.k = k;
             r.inv_n = ldexp(1.0, -s->n);
             r.mu_out = s->sc.mu + s->mu_slot;
-            r.acc = (unsigned long long *)s->rg_mem;
-            r.counter = r.acc + (size_t)2 * kRgWords * kRgLine;
-            r.side = (double2 *)((char *)s->rg_mem + kRgAccBytes);
+            r.region = (unsigned long long *)s->rg_mem;
             r.status = s->sc.status;
             r.wait_limit = s->wait_limit;
             r.stall = s->test_stall;
             s->test_stall = 0;
-            CK(s, cudaMemsetAsync(s->rg_mem, 0, kRgAccBytes, s->stream), "grid iterator reset");
+            CK(s, cudaMemsetAsync(s->rg_mem, 0, kRgBytes, s->stream), "grid iterator reset");
             cudaError_t e = launch_resident_grid(r, s->dtype, G, gsmem, s->stream);
             if (e == cudaSuccess) {
                 s->mu_valid = true;

@@ -119,16 +119,12 @@ struct ResArgs {
 // false if the state does not fit one cluster's shared memory
 bool resident_plan(int n, grover_dtype dt, unsigned *C, uint32_t *slice_vecs, size_t *smem);
 cudaError_t launch_resident(const ResArgs &a, grover_dtype dt, unsigned C, size_t smem, cudaStream_t st);
-// Grid-wide variant (cooperative launch, one CTA per SM, partials exchanged
-// through limb accumulators and an arrival counter in global memory).
+// Grid-wide variant (cooperative launch, one CTA per SM, exact partials
+// exchanged through global memory, grid_exchange.cuh).
 constexpr size_t kRgSmemMax = 226 * 1024;  // dynamic shared memory per CTA
-constexpr int kRgWords = 7;                // 3 + 3 limbs and a side-sum count per parity
-constexpr int kRgLine = 16;                // 64-bit words per 128-byte line
 constexpr int kRgMaxGrid = 512;
-// Layout of the handle's grid-iterator region (zeroed before every launch):
-// accumulators [2][kRgWords] lines, counter line, side sums [2][kRgMaxGrid].
-constexpr size_t kRgAccBytes = sizeof(unsigned long long) * kRgLine * (2 * kRgWords + 1);
-constexpr size_t kRgBytes = kRgAccBytes + sizeof(double2) * 2 * kRgMaxGrid;
+// exchange region of two sums: word sets, a spare line, side slots for 512 CTAs
+constexpr size_t kRgBytes = sizeof(unsigned long long) * 16 * (2 * 7 + 1) + sizeof(double) * 2 * kRgMaxGrid * 2;
 struct ResGridArgs {
     void *amps;
     uint64_t nvec;          // 16-byte vectors in the state
@@ -137,11 +133,9 @@ struct ResGridArgs {
     uint64_t k;
     double inv_n;
     MeanSlot *mu_out;
-    unsigned long long *acc;      // [2][kRgWords] accumulators, kRgLine apart
-    unsigned long long *counter;  // arrivals
-    double2 *side;          // [2][grid] FP64 side sums
+    unsigned long long *region;  // exchange region (kRgBytes, zeroed before the launch)
     int *status;            // set to 3 if a wait runs out
-    long long wait_limit;   // polls of the counter before giving up
+    long long wait_limit;   // polls before giving up
     int stall;              // test hook: CTA 0 never reports its first partial
 };
 bool resident_grid_plan(int n, grover_dtype dt, int sm_count, unsigned *G, uint32_t *slice_vecs, size_t *smem);

@@ -28,6 +28,7 @@
 #include <cooperative_groups.h>
 
 #include "fixed_sum.cuh"
+#include "grid_exchange.cuh"
 #include "grover_internal.cuh"
 
 namespace grv {
@@ -251,37 +252,16 @@ __global__ void __launch_bounds__(kResThreads) k_resident_cluster(ResArgs a) {
 // ---- grid-wide variant ----------------------------------------------------------------
 // The same iteration over all SMs: a cooperative launch of G CTAs (one per SM,
 // all co-resident), CTA r keeping vectors [r*L, min((r+1)*L, nvec)) in shared
-// memory.  There is no hardware barrier across the grid, so the partials meet
-// in global memory: each CTA adds its exact 128-bit partials, split into
-// 43-bit limbs, into six 64-bit accumulators (integer adds: exact and
-// independent of the order), then adds 1 to an arrival counter with release
-// semantics.  One thread per CTA polls the counter with acquire loads (at most
-// wait_limit polls; the counter was zeroed before the launch and reads
-// G * (t + 2) once iteration t is in), reads the six accumulators and
-// rebuilds the total, so every CTA holds the bitwise identical mean.  Each
-// accumulator has its own 128-byte line (the adds of different words do not
-// queue behind one another).  Accumulators are double buffered by iteration
-// parity and never reset within a launch: a CTA takes the difference from
-// what it read two iterations earlier.  A CTA adds into a parity set again
-// only after the counter shows every CTA's next partial, which each CTA adds
-// only after it has read the set.  FP64 side sums (values outside the fixed-
-// point window) go to per-CTA slots, added in rank order when a seventh
-// accumulator shows that some CTA had any.  A wait that runs out sets
-// *status = 3 and the CTA leaves the loop (the others then run out too).
+// memory.  There is no hardware barrier across the grid, so the exact CTA
+// partials meet in global memory through grid_exchange.cuh: limb sums and
+// arrival counts share 64-bit words, one thread per CTA polls them (bounded)
+// and rebuilds the exact total, so every CTA holds the bitwise identical mean.
+// A wait that runs out sets *status = 3 and the CTA leaves the loop (the
+// others then run out too).
+static_assert(kRgBytes >= GxLayout<2>::kAccBytes + GxLayout<2>::side_bytes(kRgMaxGrid),
+              "the grid iterator's exchange region is too small");
 constexpr int kRgThreads = 512;
 constexpr int kRgWarps = kRgThreads / 32;
-
-__device__ __forceinline__ void red_add_u64(unsigned long long *p, unsigned long long v) {
-    asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ void red_release_add_u64(unsigned long long *p, unsigned long long v) {
-    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
 
 template <class T>
 __global__ void __launch_bounds__(kRgThreads, 1) k_resident_grid(ResGridArgs a) {
@@ -300,7 +280,7 @@ __global__ void __launch_bounds__(kRgThreads, 1) k_resident_grid(ResGridArgs a) 
     uint32_t *fm = reinterpret_cast<uint32_t *>(smem + (size_t)a.slice_vecs * sizeof(V));
     __shared__ unsigned long long wint[kRgWarps][4];
     __shared__ double wside[kRgWarps][2];
-    __shared__ unsigned long long s_prev[2][kRgWords];
+    __shared__ unsigned long long s_prev[2][GxLayout<2>::W];
     __shared__ MeanSlot s_mu;
     __shared__ int s_abort;
 
@@ -309,7 +289,7 @@ __global__ void __launch_bounds__(kRgThreads, 1) k_resident_grid(ResGridArgs a) 
     for (uint32_t j = threadIdx.x; j < nv; j += kRgThreads) sl[j] = g[j];
     for (uint32_t w = threadIdx.x; w < nwords; w += kRgThreads) fm[w] = 0u;
     if (threadIdx.x == 0) s_abort = 0;
-    if (threadIdx.x < 2 * kRgWords) s_prev[threadIdx.x / kRgWords][threadIdx.x % kRgWords] = 0ull;
+    if (threadIdx.x < 2 * GxLayout<2>::W) s_prev[threadIdx.x / GxLayout<2>::W][threadIdx.x % GxLayout<2>::W] = 0ull;
     __syncthreads();
     if (a.mk.mode == MARK_LIST) {
         for (uint64_t i = threadIdx.x; i < a.mk.m; i += kRgThreads) {
@@ -422,58 +402,14 @@ __global__ void __launch_bounds__(kRgThreads, 1) k_resident_grid(ResGridArgs a) 
             }
             const bool withhold = a.stall && t == -1 && rank == 0;  // test hook: this partial never arrives
             if (lane == 0) {
-                unsigned long long *acc = a.acc + (size_t)par * kRgWords * kRgLine;
-                if (!withhold) {
-                    // 43-bit limbs of the two's complement partials: 152 of them
-                    // sum to less than 2^51, so the 64-bit adds cannot carry out
-                    const u128 lm = ((u128)1 << 43) - 1;
-                    red_add_u64(acc + 0 * kRgLine, (unsigned long long)(r & lm));
-                    red_add_u64(acc + 1 * kRgLine, (unsigned long long)((r >> 43) & lm));
-                    red_add_u64(acc + 2 * kRgLine, (unsigned long long)(r >> 86));
-                    red_add_u64(acc + 3 * kRgLine, (unsigned long long)(i & lm));
-                    red_add_u64(acc + 4 * kRgLine, (unsigned long long)((i >> 43) & lm));
-                    red_add_u64(acc + 5 * kRgLine, (unsigned long long)(i >> 86));
-                    if (any_side) {
-                        a.side[(size_t)par * G + rank] = make_double2(s1, s2);
-                        red_add_u64(acc + 6 * kRgLine, 1ull);
-                    } else {
-                        a.side[(size_t)par * G + rank] = make_double2(0.0, 0.0);
-                    }
-                    red_release_add_u64(a.counter, 1ull);
-                }
-                // wait until the G partials of this iteration are in
-                const unsigned long long target = (unsigned long long)G * (unsigned long long)(t + 2);
-                long long polls = 0;
-                int to = 0;
-                while (ld_acquire_u64(a.counter) < target) {
-                    if (++polls >= a.wait_limit) {
-                        to = 1;
-                        break;
-                    }
-                }
-                s_abort = to;
-                if (!to) {
-                    // this iteration's totals: the accumulators minus what they held
-                    // two iterations ago (same parity)
-                    unsigned long long d[kRgWords];
-#pragma unroll
-                    for (int w = 0; w < kRgWords; ++w) {
-                        const unsigned long long v = __ldcg(acc + w * kRgLine);
-                        d[w] = v - s_prev[par][w];
-                        s_prev[par][w] = v;
-                    }
-                    const u128 R = (u128)d[0] + ((u128)d[1] << 43) + ((u128)d[2] << 86);
-                    const u128 I = (u128)d[3] + ((u128)d[4] << 43) + ((u128)d[5] << 86);
-                    double y1 = 0.0, y2 = 0.0;
-                    if (d[6]) {  // some CTA had out-of-window values: add its side sums in rank order
-                        for (unsigned q = 0; q < G; ++q) {
-                            const double2 v = __ldcg(a.side + (size_t)par * G + q);
-                            y1 += v.x;
-                            y2 += v.y;
-                        }
-                    }
-                    const double mr = (i192_to_double(i192_from(R)) * 0x1p-100 + y1) * a.inv_n;
-                    const double mi = (i192_to_double(i192_from(I)) * 0x1p-100 + y2) * a.inv_n;
+                const u128 v[2] = {r, i};
+                const double sdv[2] = {s1, s2};
+                double tot[2];
+                const bool ok = gx_exchange<2>(v, sdv, any_side, a.region, s_prev, t + 1, G, rank, a.wait_limit,
+                                               withhold, tot);
+                s_abort = ok ? 0 : 1;
+                if (ok) {
+                    const double mr = tot[0] * a.inv_n, mi = tot[1] * a.inv_n;
                     const double tr = 2.0 * mr, ti = 2.0 * mi;
                     const float hr = (float)tr, hi = (float)ti;
                     s_mu.mu = make_double2(mr, mi);
