@@ -110,14 +110,16 @@ typedef enum {
      *   cluster: one thread-block cluster (16 CTAs x 200 KiB: n <= 18
      *            complex64, n <= 17 complex128), partials exchanged through
      *            distributed shared memory;
-     *   grid:    one CTA per SM (cooperative launch; 152 x 226 KiB on GB300:
-     *            n <= 22 complex64, n <= 21 complex128), partials added as
-     *            integer limbs into global accumulators, an arrival counter
-     *            with bounded waits (a wait that runs out sets the status
-     *            word: GROVER_ETIMEOUT at grover_sync).
-     *   -1 (default): the cluster iterator for n <= 16 (complex64) or n <= 14
-     *                 (complex128); the grid iterator for 17 <= n <= 22
-     *                 (complex64) or 15 <= n <= 21 (complex128); else one
+     *   grid:    up to one CTA per SM (cooperative launch; 152 x 226 KiB on
+     *            GB300: n <= 22 complex64, n <= 21 complex128; small states
+     *            use a quarter or half of the SMs, since the exchange costs
+     *            more with more CTAs), partials added as integer limbs into
+     *            global words that also count the arrivals, bounded waits (a
+     *            wait that runs out sets the status word: GROVER_ETIMEOUT at
+     *            grover_sync).
+     *   -1 (default): the cluster iterator for n <= 12 (complex64) or n <= 11
+     *                 (complex128); the grid iterator for 13 <= n <= 22
+     *                 (complex64) or 12 <= n <= 21 (complex128); else one
      *                 fused pass per iteration (the faster choice at each n
      *                 as measured on GB300);
      *    0: always one fused pass per iteration;

@@ -96,7 +96,8 @@ __device__ __forceinline__ I192 warp_sum_i192(I192 v) {
 // Rounds a 192-bit integer to the nearest double: the top 64 significant bits
 // with the remaining bits folded into the lowest one (a sticky bit below the
 // rounding position), converted with round to nearest, then scaled exactly.
-__device__ __forceinline__ double i192_to_double(I192 x) {
+// Scaled by 2^e (folded into the exponent; the result must stay normal).
+__device__ __forceinline__ double i192_to_double(I192 x, int e = 0) {
     const bool neg = (long long)x.w2 < 0;
     if (neg) {
         x.w0 = ~x.w0;
@@ -121,8 +122,59 @@ __device__ __forceinline__ double i192_to_double(I192 x) {
         top = x.w0;
         rest = 0;
     }
-    const double v = __ull2double_rn(top | (rest != 0ull ? 1ull : 0ull)) * __hiloint2double((1023 + shift) << 20, 0);
+    const double v = __ull2double_rn(top | (rest != 0ull ? 1ull : 0ull)) * __hiloint2double((1023 + shift + e) << 20, 0);
     return neg ? -v : v;
+}
+
+// a != 0 shifted left so that bit 127 is set: returns the shift, H:L the result.
+__device__ __forceinline__ int norm128(u128 a, unsigned long long &H, unsigned long long &L) {
+    const unsigned long long hi = (unsigned long long)(a >> 64), lo = (unsigned long long)a;
+    if (hi) {
+        const int lz = __clzll((long long)hi);
+        H = lz ? (hi << lz) | (lo >> (64 - lz)) : hi;
+        L = lo << lz;
+        return lz;
+    }
+    const int lz = __clzll((long long)lo);
+    H = lo << lz;
+    L = 0;
+    return 64 + lz;
+}
+
+// Rounds a normalised H:L to its top 24 bits (ties to even): returns m, set
+// up when the rounding went up (m may then reach 2^24).
+__device__ __forceinline__ uint32_t top24_rn(unsigned long long H, unsigned long long L, bool &up) {
+    const uint32_t m = (uint32_t)(H >> 40);
+    up = ((H >> 39) & 1ull) && ((H & ((1ull << 39) - 1)) | L | (m & 1u));
+    return m + (up ? 1u : 0u);
+}
+
+// x * 2^s for a signed 128-bit integer x as an unevaluated float pair:
+// hi = RN(x 2^s), lo = RN(x 2^s - hi), ties to even.  Integer work only, the
+// float bits assembled directly (on the GB300 a single FP64 operation costs
+// about as much latency as this whole routine).  Every nonzero value involved
+// must be a normal float: the caller keeps s >= -126 and |x| 2^s < 2^127.
+__device__ __forceinline__ float2 fix_to_f32_pair(u128 x, int s) {
+    if (x == 0) return make_float2(0.f, 0.f);
+    const uint32_t sign = (uint32_t)((unsigned long long)(x >> 64) >> 63) << 31;
+    unsigned long long H, L;
+    const int lz = norm128(sign ? (u128)0 - x : x, H, L);
+    bool up;
+    const uint32_t m = top24_rn(H, L, up);
+    // a float m * 2^E with 2^23 <= m <= 2^24 has the bits ((E + 149) << 23) + m
+    const uint32_t hb = ((uint32_t)(104 - lz + s + 149) << 23) + m;
+    // |x| - hi in units of the normalised frame (below 2^104, at most 2^103 after rounding up)
+    u128 r = ((u128)(H & ((1ull << 40) - 1)) << 64) | L;
+    if (up) r = ((u128)1 << 104) - r;
+    uint32_t lb = 0;
+    if (r != 0) {
+        unsigned long long H2, L2;
+        const int lz2 = norm128(r, H2, L2);
+        bool up2;
+        const uint32_t m2 = top24_rn(H2, L2, up2);
+        lb = ((((uint32_t)(104 - lz2 - lz + s + 149) << 23) + m2) | ((up ? 1u : 0u) << 31)) ^ sign;
+    }
+    return make_float2(__uint_as_float(hb | sign), __uint_as_float(lb));
 }
 
 }  // namespace grv

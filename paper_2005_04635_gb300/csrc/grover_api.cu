@@ -448,7 +448,7 @@ grover_status grover_iterate(grover_state *s, const grover_marked *mk, uint64_t 
         // iteration, against 2.7 us for the cluster's at small n); passes
         // otherwise
         const bool c64 = s->dtype == GROVER_C64;
-        const int cluster_max = c64 ? 16 : 14, grid_min = c64 ? 17 : 15, grid_max = c64 ? 22 : 21;
+        const int cluster_max = c64 ? 12 : 11, grid_min = c64 ? 13 : 12, grid_max = c64 ? 22 : 21;
         const bool use_cluster = cluster_fits && (s->resident == 1 || (s->resident == -1 && s->n <= cluster_max));
         const bool use_grid = !use_cluster && grid_fits &&
                               (s->resident >= 1 || (s->resident == -1 && s->n >= grid_min && s->n <= grid_max));
@@ -459,6 +459,7 @@ grover_status grover_iterate(grover_state *s, const grover_marked *mk, uint64_t 
             r.mk = mk->dev;
             r.k = k;
             r.inv_n = ldexp(1.0, -s->n);
+            r.n = s->n;
             r.mu_out = s->sc.mu + s->mu_slot;
             cudaError_t e = launch_resident(r, s->dtype, C, smem, s->stream);
             if (e == cudaSuccess) {
@@ -477,6 +478,7 @@ grover_status grover_iterate(grover_state *s, const grover_marked *mk, uint64_t 
             r.mk = mk->dev;
             r.k = k;
             r.inv_n = ldexp(1.0, -s->n);
+            r.n = s->n;
             r.mu_out = s->sc.mu + s->mu_slot;
             r.region = (unsigned long long *)s->rg_mem;
             r.status = s->sc.status;

@@ -114,6 +114,7 @@ struct ResArgs {
     MarkedDev mk;
     uint64_t k;             // iterations
     double inv_n;           // 1 / N
+    int n;                  // N = 2^n (n <= 27 keeps the float means normal)
     MeanSlot *mu_out;       // mean of O c after the last iteration
 };
 // false if the state does not fit one cluster's shared memory
@@ -123,8 +124,8 @@ cudaError_t launch_resident(const ResArgs &a, grover_dtype dt, unsigned C, size_
 // exchanged through global memory, grid_exchange.cuh).
 constexpr size_t kRgSmemMax = 226 * 1024;  // dynamic shared memory per CTA
 constexpr int kRgMaxGrid = 512;
-// exchange region of two sums: word sets, a spare line, side slots for 512 CTAs
-constexpr size_t kRgBytes = sizeof(unsigned long long) * 16 * (2 * 7 + 1) + sizeof(double) * 2 * kRgMaxGrid * 2;
+// exchange region of two sums: two sets of 8 word lines, side slots for 512 CTAs
+constexpr size_t kRgBytes = sizeof(unsigned long long) * 16 * (2 * 8) + sizeof(double) * 2 * kRgMaxGrid * 2;
 struct ResGridArgs {
     void *amps;
     uint64_t nvec;          // 16-byte vectors in the state
@@ -132,6 +133,7 @@ struct ResGridArgs {
     MarkedDev mk;
     uint64_t k;
     double inv_n;
+    int n;                  // N = 2^n (n <= 27 keeps the float means normal)
     MeanSlot *mu_out;
     unsigned long long *region;  // exchange region (kRgBytes, zeroed before the launch)
     int *status;            // set to 3 if a wait runs out

@@ -63,7 +63,7 @@ __device__ __forceinline__ unsigned long long *series4(const PhaseGridArgs &a) {
 // not touch wint / wsd and must leave its results in shared memory).
 template <int NV, class Job>
 __device__ bool cta_exchange(u128 (&v)[NV], double (&sd)[NV], const PhaseGridArgs &a, unsigned long long *region,
-                             long long xi, unsigned long long (&prev)[2][3 * NV + 1], double *tot, bool withhold,
+                             long long xi, unsigned long long (&prev)[2][GxLayout<NV>::W], double *tot, bool withhold,
                              Job side_job) {
     __shared__ unsigned long long wint[kPgWarps][kNVmax][2];
     __shared__ double wsd[kPgWarps][kNVmax];
@@ -102,12 +102,13 @@ __device__ bool cta_exchange(u128 (&v)[NV], double (&sd)[NV], const PhaseGridArg
             if (any_side) ts[q] = warp_sum_d(ts[q]);
         }
         if (lane == 0) {
-            double out[NV];
+            u128 out[NV];
+            double osd[NV];
             const bool ok = gx_exchange<NV>(t, ts, any_side, region, prev, xi, gridDim.x, blockIdx.x, a.wait_limit,
-                                            withhold, out);
+                                            withhold, out, osd);
             if (ok) {
 #pragma unroll
-                for (int q = 0; q < NV; ++q) tot[q] = out[q];
+                for (int q = 0; q < NV; ++q) tot[q] = i192_to_double(i192_from(out[q]), -100) + osd[q];
             } else {
                 atomicExch(a.status, 3);
             }
@@ -184,7 +185,7 @@ __global__ void __launch_bounds__(kPgThreads, 1) k_phase_grid_fwd(PhaseGridArgs 
     __shared__ float4 s_kap;
     __shared__ float2 s_rot;
     __shared__ float2 rep[kPhaseMaxMarked];
-    __shared__ unsigned long long prev[2][3 * 2 + 1];
+    __shared__ unsigned long long prev[2][GxLayout<2>::W];
     const unsigned rank = blockIdx.x;
     float4 *sl = reinterpret_cast<float4 *>(smem);
     const uint64_t start = (uint64_t)rank * a.slice_vecs;
@@ -196,7 +197,7 @@ __global__ void __launch_bounds__(kPgThreads, 1) k_phase_grid_fwd(PhaseGridArgs 
     const float2 *g2 = static_cast<const float2 *>(a.psi);
     for (uint32_t j = threadIdx.x; j < nv; j += kPgThreads) sl[j] = g[j];
     for (uint32_t q = threadIdx.x; q < a.m; q += kPgThreads) rep[q] = g2[a.list[q]];
-    if (threadIdx.x < 2 * 7) prev[threadIdx.x / 7][threadIdx.x % 7] = 0ull;
+    if (threadIdx.x < 2 * GxLayout<2>::W) prev[threadIdx.x / GxLayout<2>::W][threadIdx.x % GxLayout<2>::W] = 0ull;
     build_mask(fm, nwords, a, start * 2, nv * 2);
     const double inv_n = ldexp(1.0, -a.n);
     bool ok = true;
@@ -279,7 +280,7 @@ __global__ void __launch_bounds__(kPgThreads, 1) k_phase_grid_bwd(PhaseGridArgs 
     __shared__ float2 s_rot;
     __shared__ double s_is, s_g;
     __shared__ float2 repp[kPhaseMaxMarked], repl[kPhaseMaxMarked];
-    __shared__ unsigned long long prev2[2][3 * 2 + 1], prev4[2][3 * 4 + 1];
+    __shared__ unsigned long long prev2[2][GxLayout<2>::W], prev4[2][GxLayout<4>::W];
     const unsigned rank = blockIdx.x;
     float4 *sp = reinterpret_cast<float4 *>(smem);
     float4 *sm = sp + a.slice_vecs;
@@ -293,8 +294,8 @@ __global__ void __launch_bounds__(kPgThreads, 1) k_phase_grid_bwd(PhaseGridArgs 
     const float2 *g2 = static_cast<const float2 *>(a.psi);
     for (uint32_t j = threadIdx.x; j < nv; j += kPgThreads) sp[j] = gp[j];
     for (uint32_t q = threadIdx.x; q < a.m; q += kPgThreads) repp[q] = g2[a.list[q]];
-    if (threadIdx.x < 2 * 7) prev2[threadIdx.x / 7][threadIdx.x % 7] = 0ull;
-    if (threadIdx.x < 2 * 13) prev4[threadIdx.x / 13][threadIdx.x % 13] = 0ull;
+    if (threadIdx.x < 2 * GxLayout<2>::W) prev2[threadIdx.x / GxLayout<2>::W][threadIdx.x % GxLayout<2>::W] = 0ull;
+    if (threadIdx.x < 2 * GxLayout<4>::W) prev4[threadIdx.x / GxLayout<4>::W][threadIdx.x % GxLayout<4>::W] = 0ull;
     build_mask(fm, nwords, a, start * 2, nv * 2);
     const double N = ldexp(1.0, a.n), inv_n = ldexp(1.0, -a.n);
     // P from the replica (every CTA), lambda~_K = -(marked psi_K) / sqrt(P)

@@ -60,16 +60,48 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// mean = (integer sum * 2^-100 + side sum) / N, rounded once for the integer part
-__device__ __forceinline__ void write_mean_slot(MeanSlot *ms, u128 r, u128 i, double sr, double si, double inv_n) {
-    const double mr = (i192_to_double(i192_from(r)) * 0x1p-100 + sr) * inv_n;
-    const double mi = (i192_to_double(i192_from(i)) * 0x1p-100 + si) * inv_n;
+// Nonzero side sums, tested on the bits (an FP64 compare would sit on the slow
+// FP64 pipe; -0.0 merely takes the FP64 route below).
+__device__ __forceinline__ bool has_side(double a, double b) {
+    return (__double_as_longlong(a) | __double_as_longlong(b)) != 0;
+}
+
+// The mean from the exact sums r, i (units 2^-100) and the side sums sr, si,
+// N = 2^n.  Without side sums, mu = RN(sum / N) straight from the integers, and
+// the complex64 update's float pair for 2 mu is RN(2 mu exact) plus the
+// rounded rest, built with integer operations only (GB300's FP64 pipe would
+// put ~1500 cycles of latency on every iteration).  With side sums (non-
+// normalised states) everything goes through FP64: (RN(r 2^-100) + sr) / N.
+__device__ __forceinline__ void write_mean_slot(MeanSlot *ms, u128 r, u128 i, double sr, double si, int n,
+                                                bool need_f32, bool need_f64) {
+    if (!has_side(sr, si)) {
+        if (need_f32) {
+            const float2 pr = fix_to_f32_pair(r, -99 - n), pi = fix_to_f32_pair(i, -99 - n);
+            ms->two32 = make_float4(pr.x, pr.y, pi.x, pi.y);
+        }
+        if (need_f64) {
+            const double tr = i192_to_double(i192_from(r), -99 - n), ti = i192_to_double(i192_from(i), -99 - n);
+            ms->two = make_double2(tr, ti);
+            ms->mu = make_double2(0.5 * tr, 0.5 * ti);
+        }
+        return;
+    }
+    const double inv_n = __hiloint2double((1023 - n) << 20, 0);
+    const double mr = (i192_to_double(i192_from(r), -100) + sr) * inv_n;
+    const double mi = (i192_to_double(i192_from(i), -100) + si) * inv_n;
     const double tr = 2.0 * mr, ti = 2.0 * mi;
     const float hr = (float)tr, hi = (float)ti;
     ms->mu = make_double2(mr, mi);
     ms->two = make_double2(tr, ti);
     ms->two32 = make_float4(hr, (float)(tr - (double)hr), hi, (float)(ti - (double)hi));
 }
+
+// Sums behind the last mean, kept by the thread that built it, so that the
+// full slot (FP64 mean included) is written once, after the last iteration.
+struct LastSums {
+    u128 r = 0, i = 0;
+    double sr = 0.0, si = 0.0;
+};
 
 template <int G, class T> __device__ __forceinline__ T pairwise(const T *v) {
     if constexpr (G == 1) return v[0];
@@ -121,6 +153,7 @@ __global__ void __launch_bounds__(kResThreads) k_resident_cluster(ResArgs a) {
     }
     __syncthreads();
 
+    LastSums last;
     // t = -1 computes the first mean, t = 0..k-1 are the iterations
     for (long long t = -1; t < (long long)a.k; ++t) {
         const bool upd = t >= 0;
@@ -189,8 +222,7 @@ __global__ void __launch_bounds__(kResThreads) k_resident_cluster(ResArgs a) {
         // CTA partial: exact integer sums, side sums (if any) in a fixed tree order
         ar = warp_sum_u128(ar);
         ai = warp_sum_u128(ai);
-        const int any_side = __syncthreads_or(sr != 0.0 || si != 0.0);
-        if (any_side) {
+        if (__any_sync(0xffffffffu, has_side(sr, si))) {
             sr = warp_sum(sr);
             si = warp_sum(si);
         }
@@ -214,6 +246,7 @@ __global__ void __launch_bounds__(kResThreads) k_resident_cluster(ResArgs a) {
             }
             r = warp_sum_u128(r);
             i = warp_sum_u128(i);
+            const int any_side = __any_sync(0xffffffffu, has_side(s1, s2));
             if (any_side) {
                 s1 = warp_sum(s1);
                 s2 = warp_sum(s2);
@@ -240,12 +273,18 @@ __global__ void __launch_bounds__(kResThreads) k_resident_cluster(ResArgs a) {
                 s1 = warp_sum(s1);
                 s2 = warp_sum(s2);
             }
-            if (lane == 0) write_mean_slot(&s_mu, r, i, s1, s2, a.inv_n);
+            if (lane == 0) {
+                write_mean_slot(&s_mu, r, i, s1, s2, a.n, APV == 2, APV == 1);
+                last = LastSums{r, i, s1, s2};
+            }
         }
         __syncthreads();
     }
     for (uint32_t j = threadIdx.x; j < nv; j += kResThreads) g[j] = sl[j];
-    if (rank == 0 && threadIdx.x == 0) *a.mu_out = s_mu;
+    if (rank == 0 && threadIdx.x == 0) {
+        write_mean_slot(&s_mu, last.r, last.i, last.sr, last.si, a.n, true, true);
+        *a.mu_out = s_mu;
+    }
     cl.sync();  // keep every CTA's partial slots alive until all have read them
 }
 
@@ -304,9 +343,9 @@ __global__ void __launch_bounds__(kRgThreads, 1) k_resident_grid(ResGridArgs a) 
     }
     __syncthreads();
 
+    LastSums last;
     for (long long t = -1; t < (long long)a.k; ++t) {
         const bool upd = t >= 0;
-        const int par = (int)((t + 1) & 1);
         T two_re = T(0), two_im = T(0), lo_re = T(0), lo_im = T(0);
         if (upd) {
             if constexpr (APV == 2) {
@@ -371,8 +410,7 @@ __global__ void __launch_bounds__(kRgThreads, 1) k_resident_grid(ResGridArgs a) 
         // CTA partial (exact), written to its slot
         ar = warp_sum_u128(ar);
         ai = warp_sum_u128(ai);
-        const int any_side = __syncthreads_or(sr != 0.0 || si != 0.0);
-        if (any_side) {
+        if (__any_sync(0xffffffffu, has_side(sr, si))) {
             sr = warp_sum(sr);
             si = warp_sum(si);
         }
@@ -396,6 +434,7 @@ __global__ void __launch_bounds__(kRgThreads, 1) k_resident_grid(ResGridArgs a) 
             }
             r = warp_sum_u128(r);
             i = warp_sum_u128(i);
+            const int any_side = __any_sync(0xffffffffu, has_side(s1, s2));
             if (any_side) {
                 s1 = warp_sum(s1);
                 s2 = warp_sum(s2);
@@ -404,17 +443,14 @@ __global__ void __launch_bounds__(kRgThreads, 1) k_resident_grid(ResGridArgs a) 
             if (lane == 0) {
                 const u128 v[2] = {r, i};
                 const double sdv[2] = {s1, s2};
-                double tot[2];
+                u128 tot[2];
+                double tsd[2];
                 const bool ok = gx_exchange<2>(v, sdv, any_side, a.region, s_prev, t + 1, G, rank, a.wait_limit,
-                                               withhold, tot);
+                                               withhold, tot, tsd);
                 s_abort = ok ? 0 : 1;
                 if (ok) {
-                    const double mr = tot[0] * a.inv_n, mi = tot[1] * a.inv_n;
-                    const double tr = 2.0 * mr, ti = 2.0 * mi;
-                    const float hr = (float)tr, hi = (float)ti;
-                    s_mu.mu = make_double2(mr, mi);
-                    s_mu.two = make_double2(tr, ti);
-                    s_mu.two32 = make_float4(hr, (float)(tr - (double)hr), hi, (float)(ti - (double)hi));
+                    write_mean_slot(&s_mu, tot[0], tot[1], tsd[0], tsd[1], a.n, APV == 2, APV == 1);
+                    last = LastSums{tot[0], tot[1], tsd[0], tsd[1]};
                 }
             }
         }
@@ -425,7 +461,10 @@ __global__ void __launch_bounds__(kRgThreads, 1) k_resident_grid(ResGridArgs a) 
         }
     }
     for (uint32_t j = threadIdx.x; j < nv; j += kRgThreads) g[j] = sl[j];
-    if (rank == 0 && threadIdx.x == 0 && !s_abort) *a.mu_out = s_mu;
+    if (rank == 0 && threadIdx.x == 0 && !s_abort) {
+        write_mean_slot(&s_mu, last.r, last.i, last.sr, last.si, a.n, true, true);
+        *a.mu_out = s_mu;
+    }
 }
 
 template <class T> cudaError_t launch_grid_t(const ResGridArgs &a, unsigned G, size_t smem, cudaStream_t st) {
@@ -500,13 +539,23 @@ bool resident_plan(int n, grover_dtype dt, unsigned *C_out, uint32_t *slice_vecs
 
 // Grid-wide variant: one CTA per SM; the slices (and their marked bitmasks)
 // must fit one CTA's shared memory.
+// Small states run on fewer, fuller CTAs: one exchange costs about 0.8 us with
+// 16-38 CTAs, 1.0 us with 76 and 1.45 us with 152 on a GB300, while the update
+// shrinks with the slice.  Measured best: complex64 a quarter of the SMs for
+// n <= 17 and half for n = 18; complex128 (slower FP64 update) half for
+// n <= 16; all SMs above.
 bool resident_grid_plan(int n, grover_dtype dt, int sm_count, unsigned *G_out, uint32_t *slice_vecs,
                         size_t *smem_out) {
     const uint64_t N = 1ull << n;
     const int apv = dt == GROVER_C64 ? 2 : 1;
     const uint64_t nvec = N / apv;
-    if (sm_count < 1 || sm_count > kRgThreads || nvec < (uint64_t)sm_count) return false;
-    const uint64_t L = (nvec + sm_count - 1) / sm_count;
+    if (sm_count < 1 || sm_count > kRgThreads) return false;
+    int ctas = sm_count;
+    if (dt == GROVER_C64 ? n <= 17 : n <= 16) ctas = sm_count / (dt == GROVER_C64 ? 4 : 2);
+    else if (dt == GROVER_C64 && n == 18) ctas = sm_count / 2;
+    if (ctas < 1) ctas = 1;
+    if (nvec < (uint64_t)ctas) return false;
+    const uint64_t L = (nvec + ctas - 1) / ctas;
     const size_t smem = (size_t)L * 16 + ((L * apv + 31) / 32) * 4;
     if (smem > kRgSmemMax) return false;
     *G_out = (unsigned)((nvec + L - 1) / L);
