@@ -361,8 +361,9 @@ grover_status grover_iterate_noalloc(void *dev_amps, int n_qubits, grover_dtype 
  * The loss is L = -log P, P = sum over marked x of |c_x|^2 after the K
  * iterations.  Complex64 states only; the marked set must be a list of 1 to
  * 256 indices (grover_marked_from_list), else GROVER_EUNSUPPORTED.  Means are
- * exact sums of the FP32 amplitudes rounded once to FP64; phase factors are
- * computed in FP64 and applied in FP32.  Where the state fits the SMs' shared
+ * exact sums of the FP32 amplitudes, rounded once; the per-iteration
+ * constants are formed in FP64 (pass path) or in float-float arithmetic of
+ * about 48 bits (on-chip path) and applied in FP32.  Where the state fits the SMs' shared
  * memory (GB300: n <= 22) and GROVER_OPT_RESIDENT is not 0, the whole sweep is
  * one cooperative launch with the state on chip (per-iteration sums exchanged
  * exactly through global memory, bounded waits: GROVER_ETIMEOUT at

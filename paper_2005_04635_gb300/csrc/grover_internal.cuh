@@ -253,6 +253,13 @@ cudaError_t launch_phase_bwd(const PhaseArgs &a, bool stream, cudaStream_t st, i
 cudaError_t launch_phase_bwd_start(const PhaseArgs &a, bool stream, cudaStream_t st, int sm_count);
 
 // ---- the phase iterator kept on chip (k_phase_grid.cu), complex64 ------------
+// Constants of one step t, as float pairs (re hi, re lo, im hi, im lo).
+struct PhaseFac {
+    float4 em1;  // e^{i phi_t} - 1
+    float4 omv;  // 1 - e^{i vphi_t}
+    float2 rot;  // e^{i phi_t} rounded to complex64
+    float2 pad;
+};
 constexpr size_t kPhaseGridSmemMax = 232448 - 8192;  // dynamic shared memory per CTA (227 KiB less static)
 struct PhaseGridArgs {
     void *psi;                  // state (forward: psi_0 -> psi_K; backward: psi_K -> psi_0)
@@ -270,11 +277,11 @@ struct PhaseGridArgs {
     int *status;                // 3 if a wait runs out
     long long wait_limit;
     int stall;                  // test hook: CTA 0 withholds its first contribution
-    const double2 *table;       // [2K]: e^{i phi_t}, e^{i vphi_t} as (cos, sin), or NULL
+    const PhaseFac *table;      // [K] per-step constants, or NULL (then formed in the sweep)
 };
 constexpr long long kPhaseTableMax = 1ll << 14;  // table entries kept in the handle's scratch
-// Fills table[2t] = e^{i phi_t}, table[2t + 1] = e^{i vphi_t} as (cos, sin) in FP64.
-cudaError_t launch_phase_table(const double *phi, const double *vphi, long long K, double2 *table, cudaStream_t st);
+// Fills table[t] from phi_t, vphi_t (FP64 sincos, then split into float pairs).
+cudaError_t launch_phase_table(const double *phi, const double *vphi, long long K, PhaseFac *table, cudaStream_t st);
 // false if the state (backward: state and adjoint) does not fit the SMs' shared memory
 bool phase_grid_plan(int n, bool backward, int sm_count, unsigned *G, uint32_t *slice_vecs, size_t *smem);
 size_t phase_grid_region_bytes(unsigned G);  // whole exchange region

@@ -32,12 +32,12 @@ struct PhaseScratch {
     unsigned *ticket;   // [1]
     double2 *partials;  // [6 * kPhaseMaxGrid]
     unsigned long long *region;  // exchange region of the on-chip sweeps
-    double2 *table;              // [2 kPhaseTableMax] phase factors of the on-chip sweeps
+    PhaseFac *table;             // [kPhaseTableMax] per-step constants of the on-chip sweeps
 };
 constexpr size_t kPhOffTicket = 256, kPhOffPartials = 512;
 constexpr size_t kPhOffRegion = kPhOffPartials + sizeof(double2) * 6 * (size_t)kPhaseMaxGrid;
 size_t ph_off_table() { return (kPhOffRegion + phase_grid_region_bytes(512) + 255) & ~(size_t)255; }
-size_t ph_bytes() { return ph_off_table() + sizeof(double2) * 2 * (size_t)kPhaseTableMax; }
+size_t ph_bytes() { return ph_off_table() + sizeof(PhaseFac) * (size_t)kPhaseTableMax; }
 static_assert(2 * sizeof(PhaseConst) <= kPhOffTicket, "phase constants overflow their slot");
 
 grover_status phase_scratch(grover_state *s, PhaseScratch *out) {
@@ -55,7 +55,7 @@ grover_status phase_scratch(grover_state *s, PhaseScratch *out) {
     out->ticket = (unsigned *)(b + kPhOffTicket);
     out->partials = (double2 *)(b + kPhOffPartials);
     out->region = (unsigned long long *)(b + kPhOffRegion);
-    out->table = (double2 *)(b + ph_off_table());
+    out->table = (PhaseFac *)(b + ph_off_table());
     return GROVER_OK;
 }
 

@@ -15,9 +15,14 @@
 // the next mean, P, and the phi gradient's sum) are then computed in every CTA
 // without communication, and the exchange carries only the full sums: forward
 // the state sum, backward the sums of the state and of the adjoint.  Every CTA
-// forms the next pass's constants itself (FP64, the same operations in every
-// CTA, so the same values); phase factors come from a table filled before the
-// launch and are loaded while the pass before runs.
+// forms the next pass's constants itself, the same operations in every CTA, so
+// the same values.  No FP64 operation sits between an exchange and the next
+// pass (each costs ~100-175 cycles of latency on the GB300): the exact integer
+// totals become float pairs with integer operations, the constants are formed
+// in float-float arithmetic, the per-step phase factors come as float pairs
+// from a table filled before the launch, and the FP64 work that remains (the
+// replica's sums, the gradients) runs in warps 1 and 2 while warp 0 waits for
+// the other CTAs.
 // The backward sweep carries lambda~ = sqrt(P) lambda, whose entries are at
 // most 1 in magnitude (|lambda~_K,x| = |psi_x| / sqrt(P) <= 1 and the sweep is
 // unitary), so its sums stay inside the fixed-point window whatever P is; the
@@ -30,10 +35,11 @@
 namespace grv {
 namespace {
 
-using ph::dcmul;
+using ph::cff_mul;
+using ph::cff_add;
+using ph::cff_pack;
 using ph::expi;
 using ph::pairwise;
-using ph::split_hilo;
 using ph::sub_hilo;
 using ph::warp_sum_d;
 
@@ -49,9 +55,6 @@ __device__ __forceinline__ float2 cmul_rn(float2 a, float2 b) {
                        __fadd_rn(__fmul_rn(a.x, b.y), __fmul_rn(a.y, b.x)));
 }
 
-// CTA reduction of NV sums, then the grid exchange by thread 0; the totals
-// land in tot (shared).  Returns false in every thread if a wait ran out (the
-// status word is set).
 // The two exchange series in the region: one of two sums (the forward sweep;
 // the backward sweep's first exchange), then one of four (the backward passes).
 __device__ __forceinline__ unsigned long long *series2(const PhaseGridArgs &a) { return a.region; }
@@ -59,12 +62,38 @@ __device__ __forceinline__ unsigned long long *series4(const PhaseGridArgs &a) {
     return a.region + (GxLayout<2>::kAccBytes + GxLayout<2>::side_bytes(512)) / sizeof(unsigned long long);
 }
 
-// side_job runs in warp 1 while warp 0 waits for the other CTAs (it must
-// not touch wint / wsd and must leave its results in shared memory).
-template <int NV, class Job>
+// Warps 0 and 1 meet at named barrier 1 (warp 1 arrives, warp 0 waits).
+__device__ __forceinline__ void pair_arrive() { asm volatile("bar.arrive 1, 64;" ::: "memory"); }
+__device__ __forceinline__ void pair_wait() { asm volatile("bar.sync 1, 64;" ::: "memory"); }
+
+// nonzero side sum, tested on the bits (an FP64 compare is slow on the GB300)
+__device__ __forceinline__ bool has_side(double v) { return __double_as_longlong(v) != 0; }
+
+// (r 2^-100 + side) / N as a float-float: from the integer alone (exact
+// rounding, integer operations) unless there is a side sum.
+__device__ __forceinline__ ph::ff mean_ff(u128 r, double side, int n) {
+    if (!has_side(side)) {
+        const float2 p = fix_to_f32_pair(r, -100 - n);
+        return ph::ff{p.x, p.y};
+    }
+    return ph::ff_of((i192_to_double(i192_from(r), -100) + side) * __hiloint2double((1023 - n) << 20, 0));
+}
+__device__ __forceinline__ double sum_d(u128 r, double side) {
+    return i192_to_double(i192_from(r), -100) + side;
+}
+
+// The CTA's NV exact sums (side sums, if any, in a fixed tree order), then the
+// grid exchange by thread 0.  Meanwhile warp 1 runs job() (it must leave its
+// results in shared memory and not touch wint / wsd) and warp 2 aside().
+// After both the exchange and job(), thread 0 runs post(T, S) with the exact
+// integer totals (units 2^-100, the same in every CTA) and their side sums;
+// post writes the next pass's constants to shared memory.  Two block barriers
+// per exchange.  Returns false in every thread if a wait ran out (the status
+// word is set and post did not run).
+template <int NV, class Job, class Aside, class Post>
 __device__ bool cta_exchange(u128 (&v)[NV], double (&sd)[NV], const PhaseGridArgs &a, unsigned long long *region,
-                             long long xi, unsigned long long (&prev)[2][GxLayout<NV>::W], double *tot, bool withhold,
-                             Job side_job) {
+                             long long xi, unsigned long long (&prev)[2][GxLayout<NV>::W], bool withhold, Job job,
+                             Aside aside, Post post) {
     __shared__ unsigned long long wint[kPgWarps][kNVmax][2];
     __shared__ double wsd[kPgWarps][kNVmax];
     __shared__ int s_ok;
@@ -73,12 +102,12 @@ __device__ bool cta_exchange(u128 (&v)[NV], double (&sd)[NV], const PhaseGridArg
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
         v[q] = warp_sum_u128(v[q]);
-        local_side |= (sd[q] != 0.0);
+        local_side |= has_side(sd[q]);
     }
-    const int any_side = __syncthreads_or(local_side);
+    const bool warp_side = __any_sync(0xffffffffu, local_side);
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
-        if (any_side) sd[q] = warp_sum_d(sd[q]);
+        if (warp_side) sd[q] = warp_sum_d(sd[q]);
         if (lane == 0) {
             wint[warp][q][0] = (unsigned long long)v[q];
             wint[warp][q][1] = (unsigned long long)(v[q] >> 64);
@@ -86,10 +115,15 @@ __device__ bool cta_exchange(u128 (&v)[NV], double (&sd)[NV], const PhaseGridArg
         }
     }
     __syncthreads();
-    if (warp == 1) side_job();
-    if (warp == 0) {
+    if (warp == 1) {
+        job();
+        pair_arrive();
+    } else if (warp == 2) {
+        aside();
+    } else if (warp == 0) {
         u128 t[NV];
         double ts[NV];
+        int side = 0;
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
             t[q] = 0;
@@ -97,21 +131,24 @@ __device__ bool cta_exchange(u128 (&v)[NV], double (&sd)[NV], const PhaseGridArg
             if (lane < kPgWarps) {
                 t[q] = ((u128)wint[lane][q][1] << 64) | wint[lane][q][0];
                 ts[q] = wsd[lane][q];
+                side |= has_side(ts[q]);
             }
+        }
+        const int any_side = __any_sync(0xffffffffu, side);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
             t[q] = warp_sum_u128(t[q]);
             if (any_side) ts[q] = warp_sum_d(ts[q]);
         }
+        u128 T[NV];
+        double S[NV];
+        bool ok = false;
+        if (lane == 0)
+            ok = gx_exchange<NV>(t, ts, any_side, region, prev, xi, gridDim.x, blockIdx.x, a.wait_limit, withhold, T, S);
+        pair_wait();
         if (lane == 0) {
-            u128 out[NV];
-            double osd[NV];
-            const bool ok = gx_exchange<NV>(t, ts, any_side, region, prev, xi, gridDim.x, blockIdx.x, a.wait_limit,
-                                            withhold, out, osd);
-            if (ok) {
-#pragma unroll
-                for (int q = 0; q < NV; ++q) tot[q] = i192_to_double(i192_from(out[q]), -100) + osd[q];
-            } else {
-                atomicExch(a.status, 3);
-            }
+            if (ok) post(T, S);
+            else atomicExch(a.status, 3);
             s_ok = ok;
         }
     }
@@ -130,21 +167,35 @@ __device__ void build_mask(uint32_t *fm, uint32_t nwords, const PhaseGridArgs &a
     __syncthreads();
 }
 
-// e^{i phi_t} and e^{i vphi_t}: from the table the launcher filled, else
-// computed here
-struct Fac {
-    double2 e, ev;
-};
-__device__ __forceinline__ Fac factors(const PhaseGridArgs &a, long long t) {
-    if (a.table) return Fac{__ldg(a.table + 2 * t), __ldg(a.table + 2 * t + 1)};
-    return Fac{expi(a.phi[t]), expi(a.vphi[t])};
+// The constants of step t from phi_t, vphi_t (FP64 sincos, then float pairs).
+__device__ PhaseFac make_fac(double phi, double vphi) {
+    const double2 e = expi(phi), ev = expi(vphi);
+    PhaseFac f;
+    f.em1 = cff_pack(ph::cff{ph::ff_of(e.x - 1.0), ph::ff_of(e.y)});
+    f.omv = cff_pack(ph::cff{ph::ff_of(1.0 - ev.x), ph::ff_of(-ev.y)});
+    f.rot = make_float2((float)e.x, (float)e.y);
+    f.pad = make_float2(0.f, 0.f);
+    return f;
+}
+// from the table the launcher filled, else formed here
+__device__ __forceinline__ PhaseFac fac_of(const PhaseGridArgs &a, long long t) {
+    if (a.table) {
+        const float4 *p = reinterpret_cast<const float4 *>(a.table + t);
+        PhaseFac f;
+        f.em1 = __ldg(p);
+        f.omv = __ldg(p + 1);
+        const float4 r = __ldg(p + 2);
+        f.rot = make_float2(r.x, r.y);
+        f.pad = make_float2(0.f, 0.f);
+        return f;
+    }
+    return make_fac(a.phi[t], a.vphi[t]);
 }
 
-__global__ void k_phase_table(const double *phi, const double *vphi, long long K, double2 *table) {
+__global__ void k_phase_table(const double *phi, const double *vphi, long long K, PhaseFac *table) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= K) return;
-    table[2 * t] = expi(phi[t]);
-    table[2 * t + 1] = expi(vphi[t]);
+    table[t] = make_fac(phi[t], vphi[t]);
 }
 
 __device__ __forceinline__ uint32_t mark2(const uint32_t *fm, uint32_t j) {
@@ -152,38 +203,40 @@ __device__ __forceinline__ uint32_t mark2(const uint32_t *fm, uint32_t j) {
     return (fm[e >> 5] >> (e & 31)) & 3u;
 }
 
-// Warp 1 sums the replica: out = (sum Re, sum Im, sum |c|^2) in FP64 from
-// exact fixed-point sums (the same value in every CTA).
-__device__ void replica_sums(const float2 *rep, uint32_t m, double *out) {
-    if ((threadIdx.x >> 5) != 1) return;
-    const int lane = threadIdx.x & 31;
+// Exact sums of a replica by one warp: Re, Im (and |c|^2 when want_p) as
+// 128-bit integers (units 2^-100) with side sums; every lane gets them.
+struct RepSums {
     u128 r = 0, i = 0, p = 0;
     double sr = 0.0, si = 0.0, sp = 0.0;
+};
+__device__ RepSums replica_sums(const float2 *rep, uint32_t m, bool want_p) {
+    const int lane = threadIdx.x & 31;
+    RepSums o;
     for (uint32_t q = lane; q < m; q += 32) {
         const float2 c = rep[q];
-        fix_add<4>(r, sr, c.x);
-        fix_add<4>(i, si, c.y);
-        fix_add<4>(p, sp, (double)c.x * c.x + (double)c.y * c.y);
+        fix_add<4>(o.r, o.sr, c.x);
+        fix_add<4>(o.i, o.si, c.y);
+        if (want_p) fix_add<4>(o.p, o.sp, (double)c.x * c.x + (double)c.y * c.y);
     }
-    r = warp_sum_u128(r);
-    i = warp_sum_u128(i);
-    p = warp_sum_u128(p);
-    sr = warp_sum_d(sr);
-    si = warp_sum_d(si);
-    sp = warp_sum_d(sp);
-    if (lane == 0) {
-        out[0] = i192_to_double(i192_from(r)) * 0x1p-100 + sr;
-        out[1] = i192_to_double(i192_from(i)) * 0x1p-100 + si;
-        out[2] = i192_to_double(i192_from(p)) * 0x1p-100 + sp;
+    o.r = warp_sum_u128(o.r);
+    o.i = warp_sum_u128(o.i);
+    if (__any_sync(0xffffffffu, has_side(o.sr) || has_side(o.si))) {
+        o.sr = warp_sum_d(o.sr);
+        o.si = warp_sum_d(o.si);
     }
+    if (want_p) {
+        o.p = warp_sum_u128(o.p);
+        o.sp = warp_sum_d(o.sp);
+    }
+    return o;
 }
 
 // ---- forward sweep -----------------------------------------------------------
 __global__ void __launch_bounds__(kPgThreads, 1) k_phase_grid_fwd(PhaseGridArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double tot[2], rs[3];
-    __shared__ float4 s_kap;
+    __shared__ float4 s_kap, s_can;
     __shared__ float2 s_rot;
+    __shared__ PhaseFac s_fac;
     __shared__ float2 rep[kPhaseMaxMarked];
     __shared__ unsigned long long prev[2][GxLayout<2>::W];
     const unsigned rank = blockIdx.x;
@@ -199,7 +252,6 @@ __global__ void __launch_bounds__(kPgThreads, 1) k_phase_grid_fwd(PhaseGridArgs 
     for (uint32_t q = threadIdx.x; q < a.m; q += kPgThreads) rep[q] = g2[a.list[q]];
     if (threadIdx.x < 2 * GxLayout<2>::W) prev[threadIdx.x / GxLayout<2>::W][threadIdx.x % GxLayout<2>::W] = 0ull;
     build_mask(fm, nwords, a, start * 2, nv * 2);
-    const double inv_n = ldexp(1.0, -a.n);
     bool ok = true;
     for (long long t = -1; t < a.K && ok; ++t) {
         const bool upd = t >= 0;
@@ -209,9 +261,6 @@ __global__ void __launch_bounds__(kPgThreads, 1) k_phase_grid_fwd(PhaseGridArgs 
             kap = s_kap;
             rot = s_rot;
         }
-        // the next pass's phase factors, loaded while this pass runs
-        Fac fac{make_double2(1.0, 0.0), make_double2(1.0, 0.0)};
-        if (threadIdx.x == 0 && t + 1 < a.K) fac = factors(a, t + 1);
         u128 v[2] = {0, 0};
         double sd[2] = {0.0, 0.0};
         for (uint32_t j0 = threadIdx.x; j0 < nv; j0 += kU * kPgThreads) {
@@ -241,33 +290,38 @@ __global__ void __launch_bounds__(kPgThreads, 1) k_phase_grid_fwd(PhaseGridArgs 
             fix_add<4>(v[0], sd[0], pairwise<2 * kU>(gr));
             fix_add<4>(v[1], sd[1], pairwise<2 * kU>(gi));
         }
-        const bool withhold = a.stall && t == -1 && rank == 0;
-        // while the exchange waits: the replica of the marked amplitudes goes
-        // through the same update, and its sums are taken
+        const long long nxt = t + 1;
+        const bool last = nxt >= a.K;
+        // warp 1, while the exchange waits: the replica of the marked
+        // amplitudes goes through the same update; its sum A gives the oracle
+        // term (e^{i phi} - 1) A / N of the next mean (float pairs)
         auto job = [&]() {
             if (upd)
                 for (uint32_t q = threadIdx.x & 31; q < a.m; q += 32) rep[q] = sub_hilo(cmul_rn(rep[q], rot), kap);
             __syncwarp();
-            replica_sums(rep, a.m, rs);
-        };
-        ok = cta_exchange<2>(v, sd, a, series2(a), t + 1, prev, tot, withhold, job);
-        if (!ok) break;
-        if (threadIdx.x == 0) {
-            const long long nxt = t + 1;
-            if (nxt < a.K) {
-                // mean of O(phi_{t+1}) c: S + (e^{i phi} - 1) A, over N
-                const double2 e = fac.e, ev = fac.ev;
-                const double cr = (e.x - 1.0) * rs[0] - e.y * rs[1];
-                const double ci = (e.x - 1.0) * rs[1] + e.y * rs[0];
-                const double2 mu = make_double2((tot[0] + cr) * inv_n, (tot[1] + ci) * inv_n);
-                s_kap = split_hilo(dcmul(make_double2(1.0 - ev.x, -ev.y), mu));
-                s_rot = make_float2((float)e.x, (float)e.y);
-            } else if (rank == 0 && a.stats) {
-                a.stats[0] = rs[2];
-                a.stats[1] = -log(rs[2]);
+            const RepSums rs = replica_sums(rep, a.m, last);
+            if ((threadIdx.x & 31) == 0) {
+                if (!last) {
+                    const PhaseFac f = fac_of(a, nxt);
+                    s_fac = f;
+                    const ph::cff A{mean_ff(rs.r, rs.sr, a.n), mean_ff(rs.i, rs.si, a.n)};
+                    s_can = cff_pack(cff_mul(ph::cff_unpack(f.em1), A));
+                } else if (rank == 0 && a.stats) {
+                    const double P = sum_d(rs.p, rs.sp);
+                    a.stats[0] = P;
+                    a.stats[1] = -log(P);
+                }
             }
-        }
-        __syncthreads();
+        };
+        // thread 0: mean of O(phi_{t+1}) c = S / N + (e^{i phi} - 1) A / N, and
+        // the diffusion constant (1 - e^{i vphi}) times it
+        auto post = [&](const u128 (&T)[2], const double (&S)[2]) {
+            if (last) return;
+            const ph::cff mu = cff_add(ph::cff{mean_ff(T[0], S[0], a.n), mean_ff(T[1], S[1], a.n)}, ph::cff_unpack(s_can));
+            s_kap = cff_pack(cff_mul(ph::cff_unpack(s_fac.omv), mu));
+            s_rot = s_fac.rot;
+        };
+        ok = cta_exchange<2>(v, sd, a, series2(a), t + 1, prev, a.stall && t == -1 && rank == 0, job, [] {}, post);
     }
     for (uint32_t j = threadIdx.x; j < nv; j += kPgThreads) g[j] = sl[j];
 }
@@ -275,10 +329,17 @@ __global__ void __launch_bounds__(kPgThreads, 1) k_phase_grid_fwd(PhaseGridArgs 
 // ---- backward sweep ----------------------------------------------------------
 __global__ void __launch_bounds__(kPgThreads, 1) k_phase_grid_bwd(PhaseGridArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double tot[4], rs[3];
     __shared__ float4 s_kp, s_kl;
     __shared__ float2 s_rot;
-    __shared__ double s_is, s_g;
+    __shared__ double s_is;
+    __shared__ PhaseFac s_fac;
+    __shared__ RepSums s_rs;
+    // an exchange's totals, for the vphi gradient warp 2 computes during the
+    // next exchange (rank 0); two slots by exchange parity, so that a post
+    // never overwrites what a running aside reads
+    __shared__ unsigned long long s_pend[2][4][2];
+    __shared__ double s_pend_sd[2][4];
+    __shared__ long long s_pend_t[2];
     __shared__ float2 repp[kPhaseMaxMarked], repl[kPhaseMaxMarked];
     __shared__ unsigned long long prev2[2][GxLayout<2>::W], prev4[2][GxLayout<4>::W];
     const unsigned rank = blockIdx.x;
@@ -296,12 +357,14 @@ __global__ void __launch_bounds__(kPgThreads, 1) k_phase_grid_bwd(PhaseGridArgs 
     for (uint32_t q = threadIdx.x; q < a.m; q += kPgThreads) repp[q] = g2[a.list[q]];
     if (threadIdx.x < 2 * GxLayout<2>::W) prev2[threadIdx.x / GxLayout<2>::W][threadIdx.x % GxLayout<2>::W] = 0ull;
     if (threadIdx.x < 2 * GxLayout<4>::W) prev4[threadIdx.x / GxLayout<4>::W][threadIdx.x % GxLayout<4>::W] = 0ull;
+    if (threadIdx.x < 2) s_pend_t[threadIdx.x] = -1;
     build_mask(fm, nwords, a, start * 2, nv * 2);
     const double N = ldexp(1.0, a.n), inv_n = ldexp(1.0, -a.n);
     // P from the replica (every CTA), lambda~_K = -(marked psi_K) / sqrt(P)
-    replica_sums(repp, a.m, rs);
-    __syncthreads();
-    if (threadIdx.x == 0) s_is = 1.0 / sqrt(rs[2]);
+    if ((threadIdx.x >> 5) == 1) {
+        const RepSums rs = replica_sums(repp, a.m, true);
+        if ((threadIdx.x & 31) == 0) s_is = 1.0 / sqrt(sum_d(rs.p, rs.sp));
+    }
     __syncthreads();
     const double is = s_is;
     for (uint32_t q = threadIdx.x; q < a.m; q += kPgThreads)
@@ -346,28 +409,35 @@ __global__ void __launch_bounds__(kPgThreads, 1) k_phase_grid_bwd(PhaseGridArgs 
             fix_add<4>(v[0], sd[0], pairwise<2 * kU>(gr));
             fix_add<4>(v[1], sd[1], pairwise<2 * kU>(gi));
         }
-        ok = cta_exchange<2>(v, sd, a, series2(a), 0, prev2, tot, a.stall && rank == 0,
-                             [&]() { replica_sums(repl, a.m, rs); });
+        auto job = [&]() {
+            const RepSums rs = replica_sums(repl, a.m, false);
+            if ((threadIdx.x & 31) == 0) {
+                s_rs = rs;
+                if (a.K > 0) s_fac = fac_of(a, a.K - 1);
+            }
+        };
+        auto post = [&](const u128 (&T)[2], const double (&S)[2]) {
+            if (a.K == 0) return;
+            if (rank == 0) {
+                const double2 mp = make_double2(sum_d(T[0], S[0]) * inv_n, sum_d(T[1], S[1]) * inv_n);
+                const double2 ml = make_double2(sum_d(s_rs.r, s_rs.sr) * inv_n, sum_d(s_rs.i, s_rs.si) * inv_n);
+                a.grad_vphi[a.K - 1] = -2.0 * N * (ml.x * mp.y - ml.y * mp.x) * is;
+            }
+            // conjugates: e^{-i phi}, 1 - e^{-i vphi}
+            const ph::cff w = ph::cff_conj(ph::cff_unpack(s_fac.omv));
+            const ph::cff mp{mean_ff(T[0], S[0], a.n), mean_ff(T[1], S[1], a.n)};
+            const ph::cff ml{mean_ff(s_rs.r, s_rs.sr, a.n), mean_ff(s_rs.i, s_rs.si, a.n)};
+            s_kp = cff_pack(cff_mul(w, mp));
+            s_kl = cff_pack(cff_mul(w, ml));
+            s_rot = make_float2(s_fac.rot.x, -s_fac.rot.y);
+        };
+        ok = cta_exchange<2>(v, sd, a, series2(a), 0, prev2, a.stall && rank == 0, job, [] {}, post);
     }
-    if (ok && threadIdx.x == 0 && a.K > 0) {
-        const double2 mp = make_double2(tot[0] * inv_n, tot[1] * inv_n);
-        const double2 ml = make_double2(rs[0] * inv_n, rs[1] * inv_n);
-        if (rank == 0) a.grad_vphi[a.K - 1] = -2.0 * N * (ml.x * mp.y - ml.y * mp.x) * is;
-        const Fac f = factors(a, a.K - 1);  // conjugates: e^{-i phi}, e^{-i vphi}
-        const double2 ev = make_double2(f.ev.x, -f.ev.y), e = make_double2(f.e.x, -f.e.y);
-        const double2 one_m = make_double2(1.0 - ev.x, -ev.y);
-        s_kp = split_hilo(dcmul(one_m, mp));
-        s_kl = split_hilo(dcmul(one_m, ml));
-        s_rot = make_float2((float)e.x, (float)e.y);
-    }
-    __syncthreads();
     // ---- the K adjoint passes (exchanges 1..K of the second counter series) ----
     long long xi = 0;
     for (long long t = a.K - 1; t >= 0 && ok; --t, ++xi) {
         const float4 kp = s_kp, kl = s_kl;
         const float2 rot = s_rot;
-        Fac fac{make_double2(1.0, 0.0), make_double2(1.0, 0.0)};
-        if (threadIdx.x == 0 && t > 0) fac = factors(a, t - 1);
         u128 v[4] = {0, 0, 0, 0};
         double sd[4] = {0.0, 0.0, 0.0, 0.0};
         for (uint32_t j0 = threadIdx.x; j0 < nv; j0 += kU * kPgThreads) {
@@ -408,8 +478,9 @@ __global__ void __launch_bounds__(kPgThreads, 1) k_phase_grid_bwd(PhaseGridArgs 
             fix_add<4>(v[2], sd[2], pairwise<2 * kU>(lr));
             fix_add<4>(v[3], sd[3], pairwise<2 * kU>(li));
         }
-        // while the exchange waits: replicas of psi and lambda~ on the marked
-        // set, and the phi gradient's sum sum_marked Im(conj(lambda~) psi)
+        // warp 1, while the exchange waits: replicas of psi and lambda~ on the
+        // marked set, the phi gradient (rank 0) from its sum
+        // sum_marked Im(conj(lambda~) psi), and the next pass's constants
         auto job = [&]() {
             u128 gs = 0;
             double gsd = 0.0;
@@ -420,29 +491,46 @@ __global__ void __launch_bounds__(kPgThreads, 1) k_phase_grid_bwd(PhaseGridArgs 
                 fix_add<4>(gs, gsd, (double)l.x * c.y - (double)l.y * c.x);
             }
             gs = warp_sum_u128(gs);
-            gsd = warp_sum_d(gsd);
-            if ((threadIdx.x & 31) == 0) s_g = i192_to_double(i192_from(gs)) * 0x1p-100 + gsd;
-        };
-        ok = cta_exchange<4>(v, sd, a, series4(a), xi, prev4, tot, false, job);
-        if (!ok) break;
-        if (threadIdx.x == 0) {
-            const double2 mp = make_double2(tot[0] * inv_n, tot[1] * inv_n);
-            const double2 ml = make_double2(tot[2] * inv_n, tot[3] * inv_n);
-            if (rank == 0) {
+            if (__any_sync(0xffffffffu, has_side(gsd))) gsd = warp_sum_d(gsd);
+            if ((threadIdx.x & 31) == 0) {
                 // dL/dphi_t = -2 Im(sum_marked conj(lambda_t) psi_t)
-                a.grad_phi[t] = -2.0 * s_g * is;
-                // dL/dvphi_{t-1} = -2 N Im(conj(<lambda_t>) <psi_t>)
-                if (t > 0) a.grad_vphi[t - 1] = -2.0 * N * (ml.x * mp.y - ml.y * mp.x) * is;
+                if (rank == 0) a.grad_phi[t] = -2.0 * sum_d(gs, gsd) * is;
+                if (t > 0) s_fac = fac_of(a, t - 1);
             }
-            if (t > 0) {
-                const double2 ev = make_double2(fac.ev.x, -fac.ev.y), e = make_double2(fac.e.x, -fac.e.y);
-                const double2 one_m = make_double2(1.0 - ev.x, -ev.y);
-                s_kp = split_hilo(dcmul(one_m, mp));
-                s_kl = split_hilo(dcmul(one_m, ml));
-                s_rot = make_float2((float)e.x, (float)e.y);
+        };
+        // warp 2 (rank 0): dL/dvphi_{s-1} = -2 N Im(conj(<lambda_s>) <psi_s>)
+        // from the totals the previous exchange left
+        const int ps = (int)((xi + 1) & 1);  // the slot the previous exchange's post filled
+        auto aside = [&]() {
+            if (rank != 0 || (threadIdx.x & 31) != 0 || s_pend_t[ps] < 0) return;
+            u128 T[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) T[q] = ((u128)s_pend[ps][q][1] << 64) | s_pend[ps][q][0];
+            const double *sdp = s_pend_sd[ps];
+            const double2 mp = make_double2(sum_d(T[0], sdp[0]) * inv_n, sum_d(T[1], sdp[1]) * inv_n);
+            const double2 ml = make_double2(sum_d(T[2], sdp[2]) * inv_n, sum_d(T[3], sdp[3]) * inv_n);
+            a.grad_vphi[s_pend_t[ps]] = -2.0 * N * (ml.x * mp.y - ml.y * mp.x) * is;
+        };
+        auto post = [&](const u128 (&T)[4], const double (&S)[4]) {
+            if (t == 0) return;
+            const ph::cff w = ph::cff_conj(ph::cff_unpack(s_fac.omv));
+            const ph::cff mp{mean_ff(T[0], S[0], a.n), mean_ff(T[1], S[1], a.n)};
+            const ph::cff ml{mean_ff(T[2], S[2], a.n), mean_ff(T[3], S[3], a.n)};
+            s_kp = cff_pack(cff_mul(w, mp));
+            s_kl = cff_pack(cff_mul(w, ml));
+            s_rot = make_float2(s_fac.rot.x, -s_fac.rot.y);
+            if (rank == 0) {
+                const int w = (int)(xi & 1);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    s_pend[w][q][0] = (unsigned long long)T[q];
+                    s_pend[w][q][1] = (unsigned long long)(T[q] >> 64);
+                    s_pend_sd[w][q] = S[q];
+                }
+                s_pend_t[w] = t - 1;
             }
-        }
-        __syncthreads();
+        };
+        ok = cta_exchange<4>(v, sd, a, series4(a), xi, prev4, false, job, aside, post);
     }
     // psi_0 (rewound) and lambda_0 = lambda~_0 / sqrt(P); after a wait that
     // ran out the results are undefined and lambda is left as it was
@@ -495,7 +583,7 @@ size_t phase_grid_region_bytes(unsigned G) {
 }
 size_t phase_grid_zero_bytes() { return phase_grid_region_bytes(512); }
 
-cudaError_t launch_phase_table(const double *phi, const double *vphi, long long K, double2 *table, cudaStream_t st) {
+cudaError_t launch_phase_table(const double *phi, const double *vphi, long long K, PhaseFac *table, cudaStream_t st) {
     if (K <= 0) return cudaSuccess;
     k_phase_table<<<(unsigned)((K + 255) / 256), 256, 0, st>>>(phi, vphi, K, table);
     return cudaGetLastError();
