@@ -572,7 +572,14 @@ def run_phase_study(args):
                  (gpu_loss(phi0, up) - gpu_loss(phi0, dn))) / (2 * h)
             fd_err = max(fd_err, abs(d - g[t]))
 
-    # 200 Adam steps
+    # 200 Adam steps, after one untimed step on copies (the optimizer's own
+    # kernels load on first use)
+    wp = dev(phi0).requires_grad_(True)
+    wv = dev(vphi0).requires_grad_(True)
+    wopt = torch.optim.Adam([wp, wv], lr=0.05)
+    wopt.zero_grad()
+    phase_search_loss(wp, wv, st, mk).backward()
+    wopt.step()
     phi = dev(phi0).requires_grad_(True)
     vphi = dev(vphi0).requires_grad_(True)
     opt = torch.optim.Adam([phi, vphi], lr=0.05)
