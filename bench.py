@@ -300,10 +300,10 @@ def run_ours(args):
             torch.cuda.synchronize()
             st.sync()
             gate_s = g0.elapsed_time(g1) / 1e3 / args.gate_iters
-            gb = 7 if eng == 1 else 8
-            passes = 2 * ((n + gb - 1) // gb)
+            groups = gate_groups(n, eng == 1)
+            passes = 2 * len(groups)
             gate[name] = {"iteration_ms": gate_s * 1e3, "value": N / gate_s, "passes_per_iteration": passes,
-                          "group_bits": gb, "hbm_gbs": passes * 2 * BYTES_PER_AMP[dtype] * N / gate_s / 1e9,
+                          "group_bits": groups, "hbm_gbs": passes * 2 * BYTES_PER_AMP[dtype] * N / gate_s / 1e9,
                           "operator_speedup": gate_s / pass_s}
         st.set_gate_engine(-1)
         # gate by gate (one pass per single-qubit gate, Fig. oracle1 oracle):
@@ -325,10 +325,9 @@ def run_ours(args):
 
     if rank != 0:
         return None
-    # the library's choice of the persistent on-chip iterator (grover.h,
-    # GROVER_OPT_RESIDENT)
-    resident = (args.path == "auto" and n <= (17 if dtype == "c64" else 15)) or \
-        (args.path == "resident" and n <= (18 if dtype == "c64" else 17))
+    # the library's choice of a persistent on-chip iterator (grover.h,
+    # GROVER_OPT_RESIDENT: cluster or grid kernel up to n = 22 / 21)
+    resident = args.path in ("auto", "resident") and n <= (22 if dtype == "c64" else 21)
     peaks, peak_src = measured_peaks()
     achieved = BYTES_PER_AMP[dtype] * 2 * N / pass_s / 1e9
     traffic = recorded_traffic(w)
@@ -355,6 +354,15 @@ def run_ours(args):
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
     return out
+
+
+def gate_groups(n, tensor_cores):
+    """Index-bit group sizes of one H^{(x)n} in grover_iterate_gate: 7-bit groups
+    from bit 0 (tensor cores), else ceil(n / 8) groups of balanced sizes."""
+    if tensor_cores:
+        return [7] * (n // 7) + ([n % 7] if n % 7 else [])
+    g = (n + 7) // 8
+    return [n // g + (1 if i < n % g else 0) for i in range(g)]
 
 
 # ---- batched: 4096 independent searches in one persistent launch --------------------------------------
@@ -712,7 +720,7 @@ def run_gate_kernels(args):
     mk = binding.Marked(n, inputs.marked_indices(n, m, seed))
     stream = torch.cuda.current_stream()
     out = {"study": "gate-kernels", "workload": f"n={n} complex64, M={m} (seed {seed}), uniform start"}
-    for name, eng, gb in (("tensor_cores", 1, 7), ("cuda_cores", 0, 8)):
+    for name, eng in (("tensor_cores", 1), ("cuda_cores", 0)):
         st = binding.State(n, "c64", stream=stream)
         st.set_gate_engine(eng)
         st.init_uniform()
@@ -720,8 +728,10 @@ def run_gate_kernels(args):
             st.iterate_gate(mk, 1)
         t = _timed_events(lambda: st.iterate_gate(mk, 1), args.steps, stream)
         st.sync()
-        passes = 2 * ((n + gb - 1) // gb)
-        out[name] = {"iteration_ms": t * 1e3, "passes": passes, "pass_gbs": passes * 16 * N / t / 1e9}
+        groups = gate_groups(n, eng == 1)
+        passes = 2 * len(groups)
+        out[name] = {"iteration_ms": t * 1e3, "groups": groups, "passes": passes,
+                     "pass_gbs": passes * 16 * N / t / 1e9}
         del st
     return out
 

@@ -211,7 +211,7 @@ grover_status grover_iterate(grover_state *s, const grover_marked *mk, uint64_t 
  * last pass of the first transform.  Engines (GROVER_OPT_GATE_ENGINE): the
  * tensor cores (complex64: 7-bit groups as dense +-1 matrix products,
  * operands split into three bf16 slices, FP32 accumulation) or CUDA cores
- * (8-bit groups, +-1 butterflies).  The result equals grover_iterate's up to
+ * (ceil(n/8) groups of balanced sizes, +-1 butterflies).  The result equals grover_iterate's up to
  * rounding (no global phase).  Invalidates the cached mean; a tensor-core wait
  * that gives up is reported by grover_sync (GROVER_ETIMEOUT). */
 grover_status grover_iterate_gate(grover_state *s, const grover_marked *mk, uint64_t k);

@@ -520,20 +520,28 @@ grover_status grover_iterate_gate(grover_state *s, const grover_marked *mk, uint
     if (grover_status st = check_state(s)) return st;
     if (grover_status st = check_marked(s, mk)) return st;
     if (k == 0) return GROVER_OK;
-    // tensor cores: complex64, 7-bit groups from bit 0 (needs n >= 13);
-    // CUDA cores: 8-bit groups, or a group the tensor-core pass does not cover
+    // tensor cores: complex64, 7-bit groups from bit 0 (needs n >= 13), the
+    // last one shorter; CUDA cores: ceil(n / 8) groups of balanced sizes (a
+    // 1-bit remainder group would cost a whole pass for one butterfly stage),
+    // and any group the tensor-core pass does not cover
     const bool tc_possible = s->dtype == GROVER_C64 && s->n >= 13;
     if (s->gate_engine == 1 && !tc_possible)
         return fail(s, GROVER_EUNSUPPORTED, "the tensor-core gate path needs a complex64 state with n >= 13");
     const bool tc = tc_possible && s->gate_engine != 0;
     const int gbits = tc ? 7 : 8;
     const int ngroups = (s->n + gbits - 1) / gbits;
+    int glo[8], gkb[8];  // n <= 33: at most 5 groups
+    for (int gi = 0, lo = 0; gi < ngroups; ++gi) {
+        const int kb = tc ? (s->n - lo < gbits ? s->n - lo : gbits) : s->n / ngroups + (gi < s->n % ngroups ? 1 : 0);
+        glo[gi] = lo;
+        gkb[gi] = kb;
+        lo += kb;
+    }
     s->mu_valid = false;
     for (uint64_t t = 0; t < k; ++t) {
         CK(s, launch_oracle(s->amps, s->n, s->dtype, mk->dev, s->stream, s->geo), "oracle launch");
         for (int pass = 0; pass < 2 * ngroups; ++pass) {
-            const int gi = pass % ngroups, lo = gbits * gi;
-            const int kb = s->n - lo < gbits ? s->n - lo : gbits;
+            const int gi = pass % ngroups, lo = glo[gi], kb = gkb[gi];
             const bool first = pass < ngroups;  // first H^{(x)n}: scaled by 2^-n in total
             const bool phase = pass == ngroups - 1;
             if (tc && tc_pass_supported(s->n, lo, kb)) {
