@@ -164,6 +164,18 @@ def kernel_source_hash():
     return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
 
 
+def pass_kernel_name(dtype, N):
+    """The iteration kernel grover_iterate runs by default (grover.h,
+    GROVER_OPT_STAGED_PASS): the staged pass for complex64 states larger than
+    half the L2, else the per-thread pass."""
+    import torch
+    l2 = torch.cuda.get_device_properties(0).L2_cache_size
+    if dtype == "c64" and N * BYTES_PER_AMP[dtype] > l2 // 2:
+        return ("k_pass_bulk (fused oracle + inversion about the mean + next-mean partial sums, "
+                "16 KiB chunks staged through shared memory by bulk copies)")
+    return "k_pass (fused oracle + inversion about the mean + next-mean partial sums)"
+
+
 def recorded_traffic(w):
     """DRAM bytes per launch of the iteration pass from a committed ncu summary,
     scaled to this workload's N; None if no summary matches the current source."""
@@ -340,7 +352,7 @@ def run_ours(args):
         "roofline": None if resident else {
             "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-            "kernel": "k_pass (fused oracle + inversion about the mean + next-mean partial sums)",
+            "kernel": pass_kernel_name(dtype, N),
             "algorithmic_bytes_per_launch": BYTES_PER_AMP[dtype] * 2 * N,
             "avg_launch_ms": pass_s * 1e3, "peak_source": f"{peak_src} hbm_gbs"},
         "iteration_us": pass_s * 1e6,

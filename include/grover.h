@@ -139,11 +139,25 @@ typedef enum {
      * the state is undefined. */
     GROVER_OPT_WAIT_LIMIT = 2,
     /* Test hook for those failure paths: 1 makes the next tensor-core pass
-     * of grover_iterate_gate withhold its MMA completion signal, or the next
+     * of grover_iterate_gate withhold its MMA completion signal, the next
      * grid persistent launch (grover_iterate, or an on-chip phase sweep)
-     * withhold CTA 0's first partial, so a wait runs out (reset to 0 once
-     * used).  Not for production use. */
-    GROVER_OPT_TEST_STALL = 3
+     * withhold CTA 0's first partial, or the next staged pass of
+     * grover_iterate withhold CTA 0's first chunk copy, so a wait runs out
+     * (reset to 0 once used).  Not for production use. */
+    GROVER_OPT_TEST_STALL = 3,
+    /* How an iteration pass of grover_iterate moves the state:
+     *   -1 (default): complex64 states larger than half the L2 cache are
+     *                 staged: CTAs stream 16 KiB chunks through two shared-
+     *                 memory buffers each with bulk copies (cp.async.bulk; on
+     *                 GB300 about 5 % more bandwidth than per-thread loads);
+     *                 complex128 and smaller states use per-thread 16-byte
+     *                 loads and stores;
+     *    0: per-thread loads and stores always;
+     *    1: staged whenever the state is a whole number of chunks (complex64
+     *       n >= 11, complex128 n >= 10).
+     * The results are the same bit for bit.  A staged copy whose wait runs
+     * out sets the status word (GROVER_ETIMEOUT at grover_sync). */
+    GROVER_OPT_STAGED_PASS = 4
 } grover_option;
 
 /* Sets an execution option of the handle (see grover_option).  GROVER_EINVAL

@@ -177,8 +177,15 @@ class State:
         """-1 automatic, 0 CUDA-core butterflies, 1 tensor cores (complex64, n >= 13)."""
         _check(lib().grover_set_option(self.handle, 1, int(value)), self.handle)
 
+    def set_staged(self, value: int):
+        """-1 automatic (states larger than half the L2 staged through shared
+        memory by bulk copies), 0 per-thread loads always, 1 staged whenever
+        the state is a whole number of 16 KiB chunks."""
+        _check(lib().grover_set_option(self.handle, 4, int(value)), self.handle)
+
     def set_option(self, opt: int, value: int):
-        """grover_set_option: 0 resident, 1 gate engine, 2 wait limit, 3 test stall."""
+        """grover_set_option: 0 resident, 1 gate engine, 2 wait limit, 3 test
+        stall, 4 staged pass."""
         _check(lib().grover_set_option(self.handle, int(opt), int(value)), self.handle)
 
     def init_uniform(self):

@@ -81,6 +81,10 @@ PassArgs pass_args(grover_state *s, const MarkedDev &mk) {
     a.ticket = s->sc.ticket;
     a.inv_n = ldexp(1.0, -s->n);
     a.stream_hint = (long long)(s->N * amp_bytes(s->dtype)) > s->geo.l2_bytes / 2;
+    a.status = s->sc.status;
+    a.wait_limit = s->wait_limit;
+    a.staged = s->staged;
+    a.stall = 0;
     return a;
 }
 
@@ -215,6 +219,7 @@ grover_status grover_create(grover_state **out, int n, grover_dtype dtype, void 
     s->sc.probs_tmp = nullptr;
     s->resident = -1;
     s->gate_engine = -1;
+    s->staged = -1;
     s->wait_limit = kDefaultWaitLimit;
     s->test_stall = 0;
     s->mu_slot = 0;
@@ -267,6 +272,10 @@ grover_status grover_set_option(grover_state *s, grover_option opt, int64_t valu
     case GROVER_OPT_TEST_STALL:
         if (value < 0 || value > 1) return fail(s, GROVER_EINVAL, "GROVER_OPT_TEST_STALL takes 0 or 1");
         s->test_stall = (int)value;
+        return GROVER_OK;
+    case GROVER_OPT_STAGED_PASS:
+        if (value < -1 || value > 1) return fail(s, GROVER_EINVAL, "option %d takes -1, 0 or 1", (int)opt);
+        s->staged = (int)value;
         return GROVER_OK;
     }
     return fail(s, GROVER_EINVAL, "unknown option %d", (int)opt);
@@ -503,6 +512,8 @@ grover_status grover_iterate(grover_state *s, const grover_marked *mk, uint64_t 
     if (grover_status st = ensure_mean(s, mk->dev, mk->id)) return st;
     for (uint64_t t = 0; t < k; ++t) {
         PassArgs a = pass_args(s, mk->dev);
+        a.stall = s->test_stall;  // test hook, taken by the first pass (staged passes only)
+        s->test_stall = 0;
         cudaError_t e = launch_pass(a, s->dtype, s->acc, s->stream, s->geo);
         if (e != cudaSuccess) {
             s->mu_valid = false;
@@ -679,7 +690,8 @@ grover_status grover_sync(grover_state *s) {
         if (status == 4)
             return fail(s, GROVER_ECUDA, "tensor-core pass skipped: its staging buffer is not 1024-byte aligned");
         return fail(s, GROVER_ETIMEOUT, "a bounded device-side wait gave up (status %d: %s)", status,
-                    status == 3 ? "grid persistent iterator" : "tensor-core pass");
+                    status == 3 ? "grid persistent iterator"
+                    : status == 5 ? "staged iteration pass" : "tensor-core pass");
     }
     return GROVER_OK;
 }

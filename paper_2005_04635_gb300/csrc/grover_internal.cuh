@@ -73,6 +73,10 @@ struct PassArgs {
     unsigned *ticket;
     double inv_n;           // 1 / N
     bool stream_hint;       // state larger than L2: streaming cache hints
+    int *status;            // device status word (5: a staged copy's wait ran out), or NULL
+    long long wait_limit;   // polls of a bounded wait
+    int staged;             // -1 staged above L2 / 2, 0 never, 1 whenever whole chunks
+    int stall;              // test hook: CTA 0 of a staged pass withholds its first copy
 };
 
 // ---- launchers (k_stream.cu) ---------------------------------------------
@@ -317,6 +321,7 @@ struct grover_state {
     grv::Scratch sc;
     int resident;           // -1 auto, 0 never, 1 required (grover_set_option)
     int gate_engine;        // -1 auto, 0 CUDA cores, 1 tensor cores (grover_set_option)
+    int staged;             // GROVER_OPT_STAGED_PASS: -1 auto, 0 never, 1 whenever possible
     long long wait_limit;   // polls of a bounded device-side wait
     int test_stall;         // test hook: the next tensor-core pass withholds its MMA signal
     int mu_slot;            // which mu[] holds the current mean

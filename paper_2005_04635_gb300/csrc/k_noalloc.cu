@@ -137,6 +137,10 @@ extern "C" grover_status grover_iterate_noalloc(void *dev_amps, int n, grover_dt
     a.ticket = ticket;
     a.inv_n = ldexp(1.0, -n);
     a.stream_hint = (long long)(N * (dtype == GROVER_C64 ? 8 : 16)) > geo.l2_bytes / 2;
+    a.status = nullptr;  // no status word: a staged wait that runs out is not reported here
+    a.wait_limit = 1ll << 22;
+    a.staged = 0;  // per-thread pass: the grid stays within the resident-CTA bound the scratch is sized for
+    a.stall = 0;
 
     // mean of O c for the first iteration, then k fused passes; FP64
     // accumulation keeps one partial-sum slot per CTA

@@ -493,6 +493,190 @@ __global__ void __launch_bounds__(kThreads) k_pass(PassArgs a) {
     }
 }
 
+// ---- the fused pass, staged through shared memory ---------------------------------------------
+// The same pass for states larger than L2, with the state moved by the bulk
+// copy engine instead of per-thread loads: CTAs stream chunks of
+// kUnroll * kThreads vectors (16 KiB, the tile of k_pass, so every thread
+// works on the same vectors and groups as there and the results are bitwise
+// those of k_pass) through kBulkStages shared-memory buffers.  Thread 0 keeps
+// the next chunk loads in flight (cp.async.bulk, completion counted on an
+// mbarrier per buffer); every thread waits for its buffer (bounded), updates
+// it in place, one block barrier, and thread 0 writes the buffer back with one
+// bulk store and refills the buffer of the chunk before, whose store has been
+// reading it meanwhile.
+// Shape, measured on GB300 (n = 29 / 32 / 33 complex64, GB/s per pass): two
+// stages and 8 CTAs launched per SM (6 resident, shared memory bounds them)
+// 6722 / 6680 / 6717 against 6386 / 6376 / 6383 with per-thread 16-byte
+// loads and stores; one CTA per SM with 4-8 stages is faster at some sizes
+// and slower at others (6789 at n = 29, 6007 at n = 33 with 6 stages).
+constexpr int kBulkStages = 2;
+constexpr int kBulkCtasPerSm = 8;
+constexpr int kBulkChunk = kThreads * kUnroll;  // vectors per chunk (16 KiB)
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *b, unsigned count) {
+    asm volatile("mbarrier.init.shared.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared.b64 _, [%0], %1;" ::"r"(smem_addr(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *b, unsigned parity) {
+    uint32_t ok;
+    asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                 : "=r"(ok) : "r"(smem_addr(b)), "r"(parity) : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, uint64_t *b) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(b)) : "memory");
+}
+__device__ __forceinline__ void bulk_store(void *dst, const void *src, unsigned bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src)),
+                 "r"(bytes) : "memory");
+}
+
+template <class T, int MARK, int ACC>
+__global__ void __launch_bounds__(kThreads) k_pass_bulk(PassArgs a) {
+    using V = typename Vec<T>::V;
+    constexpr int APV = Vec<T>::APV;
+    constexpr unsigned kBytes = kBulkChunk * sizeof(V);
+    using Acc = typename AccSel<T, ACC>::A;
+    using S = typename AccSel<T, ACC>::S;
+    extern __shared__ __align__(128) unsigned char stage[];  // [kBulkStages][kBytes]
+    __shared__ __align__(8) uint64_t bar[kBulkStages];
+    __shared__ int s_bad;
+
+    V *amps = static_cast<V *>(a.amps);
+    const uint64_t G = gridDim.x, nchunks = a.nvec / kBulkChunk;
+    const uint64_t mine = blockIdx.x < nchunks ? (nchunks - 1 - blockIdx.x) / G + 1 : 0;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kBulkStages; ++s) mbar_init(&bar[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_bad = 0;
+    }
+    ListCursor cur;
+    if (MARK == MARK_LIST) cur.init(a.mk.list, a.mk.m, ((uint64_t)blockIdx.x * kBulkChunk + threadIdx.x) * APV);
+    __syncthreads();
+
+    griddep_wait();  // previous pass: its stores and its mean are visible
+    griddep_launch_dependents();
+    uint64_t issued = 0;  // chunk loads issued (thread 0)
+    if (threadIdx.x == 0)
+        for (; issued < (uint64_t)kBulkStages && issued < mine; ++issued) {
+            mbar_expect_tx(&bar[issued], kBytes);
+            if (a.stall && blockIdx.x == 0 && issued == 0) continue;  // test hook: this copy never comes
+            bulk_load(stage + issued * kBytes, amps + (blockIdx.x + issued * G) * kBulkChunk, kBytes, &bar[issued]);
+        }
+
+    T two_re = T(0), two_im = T(0), lo_re = T(0), lo_im = T(0);
+    if constexpr (APV == 2) {
+        const float4 h = a.mu_in->two32;
+        two_re = h.x;
+        lo_re = h.y;
+        two_im = h.z;
+        lo_im = h.w;
+    } else {
+        const double2 t2 = a.mu_in->two;
+        two_re = t2.x;
+        two_im = t2.y;
+    }
+    auto upd = [&](T x, T two, T lo) -> T {
+        if constexpr (APV == 2) return (two - x) + lo;
+        else return two - x;
+    };
+
+    constexpr int G8 = kUnroll * APV;
+    Acc acc;
+    uint64_t i = 0;
+    for (; i < mine; ++i) {
+        const int s = (int)(i % kBulkStages);
+        const unsigned parity = (unsigned)((i / kBulkStages) & 1);
+        const uint64_t base = (blockIdx.x + i * G) * kBulkChunk;
+        // the marked flags need no data: take them before waiting
+        uint32_t f[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const uint64_t v = base + (uint64_t)u * kThreads + threadIdx.x;
+            f[u] = 0;
+            if (MARK == MARK_BITS) f[u] = mask_bits<APV>(a.mk.words, v * APV);
+            if (MARK == MARK_LIST) f[u] = cur.template bits<APV>(v * APV);
+        }
+        for (long long polls = 0; !mbar_try_wait(&bar[s], parity);)
+            if (++polls >= a.wait_limit) {
+                s_bad = 1;  // seen by every thread after the barrier below
+                break;
+            }
+        V *buf = reinterpret_cast<V *>(stage + (size_t)s * kBytes);
+        T gr[G8], gi[G8];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            V c = buf[u * kThreads + threadIdx.x];
+            if constexpr (APV == 2) {
+                const uint32_t f0 = f[u] & 1u, f1 = f[u] >> 1;
+                c.x = upd(flip(c.x, f0), two_re, lo_re);
+                c.y = upd(flip(c.y, f0), two_im, lo_im);
+                c.z = upd(flip(c.z, f1), two_re, lo_re);
+                c.w = upd(flip(c.w, f1), two_im, lo_im);
+                buf[u * kThreads + threadIdx.x] = c;
+                gr[2 * u] = flip(c.x, f0);
+                gi[2 * u] = flip(c.y, f0);
+                gr[2 * u + 1] = flip(c.z, f1);
+                gi[2 * u + 1] = flip(c.w, f1);
+            } else {
+                const uint32_t f0 = f[u];
+                c.x = upd(flip(c.x, f0), two_re, lo_re);
+                c.y = upd(flip(c.y, f0), two_im, lo_im);
+                buf[u * kThreads + threadIdx.x] = c;
+                gr[u] = flip(c.x, f0);
+                gi[u] = flip(c.y, f0);
+            }
+        }
+        acc.template add_group<G8>(gr, gi);
+        // this thread's shared-memory writes, before the bulk store reads them
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (s_bad) break;
+        if (threadIdx.x == 0) {
+            bulk_store(amps + base, buf, kBytes);
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+            // refill the buffer of the previous chunk, whose store has had a
+            // whole chunk's compute time to read it (only the newest store may
+            // still be reading)
+            if (i >= 1 && i - 1 + kBulkStages < mine) {
+                asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+                const int sp = (int)((i - 1) % kBulkStages);
+                mbar_expect_tx(&bar[sp], kBytes);
+                bulk_load(stage + (size_t)sp * kBytes, amps + (blockIdx.x + (i - 1 + kBulkStages) * G) * kBulkChunk,
+                          kBytes, &bar[sp]);
+                ++issued;
+            }
+        }
+    }
+    if (threadIdx.x == 0) {
+        asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // stores complete before the combine
+        if (s_bad) {
+            // chunk i's wait ran out: report it, and let the loads still in
+            // flight (chunks i .. issued - 1) land, bounded, before the CTA's
+            // shared memory is released
+            if (a.status) atomicExch(a.status, 5);
+            for (uint64_t j = i; j < issued; ++j)
+                for (long long polls = 0;
+                     !mbar_try_wait(&bar[j % kBulkStages], (unsigned)((j / kBulkStages) & 1));)
+                    if (++polls >= a.wait_limit) break;
+        }
+    }
+
+    if constexpr (AccSel<T, ACC>::INT) {
+        int_combine(acc.r, acc.i, acc.side_r, acc.side_i, a);
+    } else {
+        __shared__ S sm[kThreads / 32];
+        const auto val = acc_value(acc);
+        S r = block_sum((S)val.x, sm);
+        S im = block_sum((S)val.y, sm);
+        grid_combine(make_double2((double)r, (double)im), a);
+    }
+}
+
 // ---- initialisation / oracle -----------------------------------------------------------------
 template <class T> __global__ void __launch_bounds__(kThreads) k_init_uniform(void *amps, uint64_t nvec, int n) {
     using V = typename Vec<T>::V;
@@ -596,9 +780,45 @@ cudaError_t launch_pass_t(const PassArgs &a, cudaStream_t st, const Geometry &g)
     return launch(kern, grid, kThreads, st, a);
 }
 
+template <class T, int MARK, int ACC>
+cudaError_t launch_bulk_t(const PassArgs &a, cudaStream_t st, const Geometry &g) {
+    auto kern = k_pass_bulk<T, MARK, ACC>;
+    constexpr size_t smem = (size_t)kBulkStages * kBulkChunk * 16;
+    cudaError_t e = raise_smem_limit(kern, smem);
+    if (e != cudaSuccess) return e;
+    const uint64_t nchunks = a.nvec / kBulkChunk, cap = (uint64_t)g.sm_count * kBulkCtasPerSm;
+    unsigned grid = (unsigned)(nchunks < cap ? nchunks : cap);
+    if (grid > (unsigned)kMaxGrid) grid = kMaxGrid;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
 template <class T, int ACC, bool UPDATE>
 cudaError_t dispatch_mark(const PassArgs &a, cudaStream_t st, const Geometry &g) {
     const bool s = a.stream_hint;
+    // the staged pass for complex64 states larger than L2 / 2 (whole chunks
+    // only); complex128 (FP64 update, every amplitude summed exactly) keeps
+    // the per-thread pass unless asked: staged it measured 5.3 against
+    // 6.3 TB/s at n = 28, the work per byte wants more warps than two stages
+    // per CTA leave
+    const bool automatic = s && sizeof(T) == 4;
+    if (UPDATE && (a.staged == 1 || (a.staged < 0 && automatic)) && a.nvec >= (uint64_t)kBulkChunk &&
+        a.nvec % kBulkChunk == 0) {
+        switch (a.mk.mode) {
+        case MARK_LIST: return launch_bulk_t<T, MARK_LIST, ACC>(a, st, g);
+        case MARK_BITS: return launch_bulk_t<T, MARK_BITS, ACC>(a, st, g);
+        default: return launch_bulk_t<T, MARK_NONE, ACC>(a, st, g);
+        }
+    }
     switch (a.mk.mode) {
     case MARK_LIST:
         return s ? launch_pass_t<T, MARK_LIST, ACC, true, UPDATE>(a, st, g)
