@@ -505,7 +505,7 @@ __global__ void __launch_bounds__(kThreads) k_pass(PassArgs a) {
 // bulk store and refills the buffer of the chunk before, whose store has been
 // reading it meanwhile.
 // Shape, measured on GB300 (n = 29 / 32 / 33 complex64, GB/s per pass): two
-// stages and 8 CTAs launched per SM (6 resident, shared memory bounds them)
+// stages and 8 CTAs launched per SM (4 resident at 62 registers a thread)
 // 6722 / 6680 / 6717 against 6386 / 6376 / 6383 with per-thread 16-byte
 // loads and stores; one CTA per SM with 4-8 stages is faster at some sizes
 // and slower at others (6789 at n = 29, 6007 at n = 33 with 6 stages).
