@@ -126,16 +126,35 @@ __device__ __forceinline__ double i192_to_double(I192 x, int e = 0) {
     return neg ? -v : v;
 }
 
+// The float-pair conversion below also compiles for the host, where a unit
+// test checks it against exact rounding.
+__host__ __device__ __forceinline__ int clz64(unsigned long long x) {
+#ifdef __CUDA_ARCH__
+    return __clzll((long long)x);
+#else
+    return x ? __builtin_clzll(x) : 64;
+#endif
+}
+__host__ __device__ __forceinline__ float float_from_bits(uint32_t b) {
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(b);
+#else
+    float f;
+    __builtin_memcpy(&f, &b, sizeof f);
+    return f;
+#endif
+}
+
 // a != 0 shifted left so that bit 127 is set: returns the shift, H:L the result.
-__device__ __forceinline__ int norm128(u128 a, unsigned long long &H, unsigned long long &L) {
+__host__ __device__ __forceinline__ int norm128(u128 a, unsigned long long &H, unsigned long long &L) {
     const unsigned long long hi = (unsigned long long)(a >> 64), lo = (unsigned long long)a;
     if (hi) {
-        const int lz = __clzll((long long)hi);
+        const int lz = clz64(hi);
         H = lz ? (hi << lz) | (lo >> (64 - lz)) : hi;
         L = lo << lz;
         return lz;
     }
-    const int lz = __clzll((long long)lo);
+    const int lz = clz64(lo);
     H = lo << lz;
     L = 0;
     return 64 + lz;
@@ -143,7 +162,7 @@ __device__ __forceinline__ int norm128(u128 a, unsigned long long &H, unsigned l
 
 // Rounds a normalised H:L to its top 24 bits (ties to even): returns m, set
 // up when the rounding went up (m may then reach 2^24).
-__device__ __forceinline__ uint32_t top24_rn(unsigned long long H, unsigned long long L, bool &up) {
+__host__ __device__ __forceinline__ uint32_t top24_rn(unsigned long long H, unsigned long long L, bool &up) {
     const uint32_t m = (uint32_t)(H >> 40);
     up = ((H >> 39) & 1ull) && ((H & ((1ull << 39) - 1)) | L | (m & 1u));
     return m + (up ? 1u : 0u);
@@ -154,7 +173,7 @@ __device__ __forceinline__ uint32_t top24_rn(unsigned long long H, unsigned long
 // float bits assembled directly (on the GB300 a single FP64 operation costs
 // about as much latency as this whole routine).  Every nonzero value involved
 // must be a normal float: the caller keeps s >= -126 and |x| 2^s < 2^127.
-__device__ __forceinline__ float2 fix_to_f32_pair(u128 x, int s) {
+__host__ __device__ __forceinline__ float2 fix_to_f32_pair(u128 x, int s) {
     if (x == 0) return make_float2(0.f, 0.f);
     const uint32_t sign = (uint32_t)((unsigned long long)(x >> 64) >> 63) << 31;
     unsigned long long H, L;
@@ -174,7 +193,7 @@ __device__ __forceinline__ float2 fix_to_f32_pair(u128 x, int s) {
         const uint32_t m2 = top24_rn(H2, L2, up2);
         lb = ((((uint32_t)(104 - lz2 - lz + s + 149) << 23) + m2) | ((up ? 1u : 0u) << 31)) ^ sign;
     }
-    return make_float2(__uint_as_float(hb | sign), __uint_as_float(lb));
+    return make_float2(float_from_bits(hb | sign), float_from_bits(lb));
 }
 
 }  // namespace grv
