@@ -601,9 +601,10 @@ __global__ void __launch_bounds__(kThreads) k_pass_bulk(PassArgs a) {
             if (MARK == MARK_BITS) f[u] = mask_bits<APV>(a.mk.words, v * APV);
             if (MARK == MARK_LIST) f[u] = cur.template bits<APV>(v * APV);
         }
+        int timed_out = 0;
         for (long long polls = 0; !mbar_try_wait(&bar[s], parity);)
             if (++polls >= a.wait_limit) {
-                s_bad = 1;  // seen by every thread after the barrier below
+                timed_out = 1;
                 break;
             }
         V *buf = reinterpret_cast<V *>(stage + (size_t)s * kBytes);
@@ -632,10 +633,14 @@ __global__ void __launch_bounds__(kThreads) k_pass_bulk(PassArgs a) {
             }
         }
         acc.template add_group<G8>(gr, gi);
-        // this thread's shared-memory writes, before the bulk store reads them
+        // this thread's shared-memory writes, before the bulk store reads them;
+        // the barrier also tells every thread whether any wait of this chunk
+        // ran out, so all leave the loop at the same chunk
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (s_bad) break;
+        if (__syncthreads_or(timed_out)) {
+            if (threadIdx.x == 0) s_bad = 1;
+            break;
+        }
         if (threadIdx.x == 0) {
             bulk_store(amps + base, buf, kBytes);
             asm volatile("cp.async.bulk.commit_group;" ::: "memory");
