@@ -127,10 +127,11 @@ typedef enum {
      *       (GROVER_EUNSUPPORTED where neither fits);
      *    2: the grid iterator (GROVER_EUNSUPPORTED where it does not fit). */
     GROVER_OPT_RESIDENT = 0,
-    /* Engine of grover_iterate_gate's Walsh-Hadamard passes: -1 (default) the
-     * tensor cores for complex64 states with n >= 13, CUDA cores otherwise;
-     * 0 always CUDA cores; 1 the tensor cores (GROVER_EUNSUPPORTED for
-     * complex128 or n < 13). */
+    /* Engine of grover_iterate_gate's Walsh-Hadamard passes: -1 (default) and
+     * 0 CUDA cores (the passes are bandwidth-bound; on GB300 the CUDA-core
+     * passes measured 1.1-3.3x faster than the tensor-core ones at every
+     * n = 13..30); 1 the tensor cores (GROVER_EUNSUPPORTED for complex128 or
+     * n < 13). */
     GROVER_OPT_GATE_ENGINE = 1,
     /* Polls (about 0.1 us each) a bounded device-side wait makes before it
      * gives up; default 2^22.  A wait that gives up sets the device status
@@ -225,7 +226,8 @@ grover_status grover_iterate(grover_state *s, const grover_marked *mk, uint64_t 
  * last pass of the first transform.  Engines (GROVER_OPT_GATE_ENGINE): the
  * tensor cores (complex64: 7-bit groups as dense +-1 matrix products,
  * operands split into three bf16 slices, FP32 accumulation) or CUDA cores
- * (ceil(n/8) groups of balanced sizes, +-1 butterflies).  The result equals grover_iterate's up to
+ * (ceil(n/8) groups of balanced sizes, +-1 butterflies; the default).  The
+ * result equals grover_iterate's up to
  * rounding (no global phase).  Invalidates the cached mean; a tensor-core wait
  * that gives up is reported by grover_sync (GROVER_ETIMEOUT). */
 grover_status grover_iterate_gate(grover_state *s, const grover_marked *mk, uint64_t k);

@@ -174,7 +174,8 @@ class State:
         _check(lib().grover_set_option(self.handle, 0, int(value)), self.handle)
 
     def set_gate_engine(self, value: int):
-        """-1 automatic, 0 CUDA-core butterflies, 1 tensor cores (complex64, n >= 13)."""
+        """-1 automatic (CUDA cores), 0 CUDA-core butterflies, 1 tensor cores
+        (complex64, n >= 13)."""
         _check(lib().grover_set_option(self.handle, 1, int(value)), self.handle)
 
     def set_staged(self, value: int):

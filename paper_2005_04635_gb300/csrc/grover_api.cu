@@ -531,14 +531,15 @@ grover_status grover_iterate_gate(grover_state *s, const grover_marked *mk, uint
     if (grover_status st = check_state(s)) return st;
     if (grover_status st = check_marked(s, mk)) return st;
     if (k == 0) return GROVER_OK;
-    // tensor cores: complex64, 7-bit groups from bit 0 (needs n >= 13), the
-    // last one shorter; CUDA cores: ceil(n / 8) groups of balanced sizes (a
-    // 1-bit remainder group would cost a whole pass for one butterfly stage),
-    // and any group the tensor-core pass does not cover
+    // CUDA cores (default; measured faster than the tensor cores at every n):
+    // ceil(n / 8) groups of balanced sizes (a 1-bit remainder group would cost
+    // a whole pass for one butterfly stage); tensor cores (asked for):
+    // complex64, 7-bit groups from bit 0 (needs n >= 13), the last one
+    // shorter, CUDA cores for any group the tensor-core pass does not cover
     const bool tc_possible = s->dtype == GROVER_C64 && s->n >= 13;
     if (s->gate_engine == 1 && !tc_possible)
         return fail(s, GROVER_EUNSUPPORTED, "the tensor-core gate path needs a complex64 state with n >= 13");
-    const bool tc = tc_possible && s->gate_engine != 0;
+    const bool tc = tc_possible && s->gate_engine == 1;
     const int gbits = tc ? 7 : 8;
     const int ngroups = (s->n + gbits - 1) / gbits;
     int glo[8], gkb[8];  // n <= 33: at most 5 groups

