@@ -82,3 +82,23 @@ def test_workloads_and_optimal_counts():
     assert w["k"] == 12867 and w["n"] == 28
     assert bench.workload("n12-c128-m1")["k"] == 50
     assert bench.workload(bench.DEFAULT_WORKLOAD)["k"] == 100
+
+
+def test_gate_groups_partition_the_index_bits():
+    """The group sizes the benchmark reports for each gate engine: they cover
+    the n index bits exactly; CUDA cores use ceil(n/8) groups of sizes that
+    differ by at most one (each group above bit 0 starts at bit 4 or higher,
+    as the CUDA-core pass requires); tensor cores use 7-bit groups from bit 0
+    and a shorter last one."""
+    sys.path.insert(0, ROOT)
+    import bench
+    for n in range(1, 34):
+        cc = bench.gate_groups(n, False)
+        assert sum(cc) == n and len(cc) == (n + 7) // 8
+        assert max(cc) - min(cc) <= 1 and max(cc) <= 8
+        starts = [sum(cc[:i]) for i in range(len(cc))]
+        assert all(s == 0 or s >= 4 for s in starts)
+        tc = bench.gate_groups(n, True)
+        assert sum(tc) == n and all(g == 7 for g in tc[:-1]) and 1 <= tc[-1] <= 7
+    assert bench.gate_groups(33, False) == [7, 7, 7, 6, 6]
+    assert bench.gate_groups(33, True) == [7, 7, 7, 7, 5]
