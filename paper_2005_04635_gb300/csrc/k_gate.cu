@@ -30,7 +30,6 @@ namespace grv {
 namespace {
 
 constexpr int kGateThreads = 256;
-constexpr int kCols = 16;
 constexpr int kPad = 1;  // complex elements of padding per shared-memory row
 
 template <class T> struct C2 {
@@ -52,13 +51,18 @@ template <int LOG, class T> __device__ __forceinline__ void wht_regs(C2<T> *v) {
 }
 
 // LOW: the group starts at bit 0 (columns are consecutive blocks of 2^KB);
-// otherwise lo >= 4 (columns are 16 consecutive amplitudes).
-template <class T, int KB, bool LOW>
+// otherwise lo >= 4 (columns are COLS consecutive amplitudes).  WIDE (6-bit
+// groups above bit 0, lo >= 5): 32 columns and 3 + 3 bits per phase, so every
+// thread keeps eight loads in flight as in the 7-bit passes instead of four.
+template <class T, int KB, bool LOW, bool WIDE>
 __global__ void __launch_bounds__(kGateThreads)
 k_wht(C2<T> *amps, int lo, uint64_t ntiles, int cols, T scale, int negate_but_zero) {
-    constexpr int B = KB < 4 ? KB : 4;
+    static_assert(!WIDE || (KB == 6 && !LOW), "the wide mapping is for 6-bit groups above bit 0");
+    constexpr int kCols = WIDE ? 32 : 16;
+    constexpr int B = WIDE ? 3 : (KB < 4 ? KB : 4);
     constexpr int A = KB - B;
     constexpr int NA = 1 << A, NB = 1 << B, MIDS = 1 << KB;
+    static_assert(LOW || kCols * NB <= kGateThreads, "at most one phase-1 value row per thread");
     constexpr int ROW = kCols + kPad;
     extern __shared__ __align__(16) unsigned char smraw[];
     C2<T> *sm = reinterpret_cast<C2<T> *>(smraw);  // [MIDS][ROW]
@@ -126,11 +130,12 @@ k_wht(C2<T> *amps, int lo, uint64_t ntiles, int cols, T scale, int negate_but_ze
     }
 }
 
-template <class T, int KB, bool LOW>
-cudaError_t launch_wht_t(void *amps, int n, int lo, T scale, bool negate, cudaStream_t st, const Geometry &g) {
+template <class T, int KB, bool LOW, bool WIDE>
+cudaError_t launch_wht_w(void *amps, int n, int lo, T scale, bool negate, cudaStream_t st, const Geometry &g) {
+    constexpr int kCols = WIDE ? 32 : 16;
     constexpr int MIDS = 1 << KB;
     const size_t smem = (size_t)MIDS * (kCols + kPad) * sizeof(C2<T>);
-    auto kern = k_wht<T, KB, LOW>;
+    auto kern = k_wht<T, KB, LOW, WIDE>;
     {
         cudaError_t e = raise_smem_limit(kern, smem);
         if (e != cudaSuccess) return e;
@@ -152,6 +157,14 @@ cudaError_t launch_wht_t(void *amps, int n, int lo, T scale, bool negate, cudaSt
     const unsigned grid = (unsigned)(ntiles < cap ? ntiles : cap);
     kern<<<grid, kGateThreads, smem, st>>>(static_cast<C2<T> *>(amps), lo, ntiles, cols, scale, negate ? 1 : 0);
     return cudaGetLastError();
+}
+
+template <class T, int KB, bool LOW>
+cudaError_t launch_wht_t(void *amps, int n, int lo, T scale, bool negate, cudaStream_t st, const Geometry &g) {
+    if constexpr (KB == 6 && !LOW) {
+        if (lo >= 5) return launch_wht_w<T, KB, LOW, true>(amps, n, lo, scale, negate, st, g);
+    }
+    return launch_wht_w<T, KB, LOW, false>(amps, n, lo, scale, negate, st, g);
 }
 
 template <class T, bool LOW>
