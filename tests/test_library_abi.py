@@ -125,3 +125,25 @@ def test_null_handles_of_the_extended_calls(lib):
     assert lib.grover_batch_amps_needed(2, (ctypes.c_int * 2)(5, 27)) == 0  # n above 26
     assert lib.grover_batch_amps_needed(2, (ctypes.c_int * 2)(5, 6)) == 32 + 64
     assert lib.grover_iterate_noalloc(None, 10, 0, None, 0, 1, None) == 1
+
+
+def header_enum(name_prefix):
+    """(name, value) pairs of the header's enum constants starting with name_prefix."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    return {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(" + name_prefix + r"[A-Z_0-9]*)\s*=\s*(\d+)", text)}
+
+
+def test_binding_option_ids_match_the_header():
+    """The option ids the Python helpers pass to grover_set_option are the
+    header's grover_option values (a renumbering would silently set the wrong
+    option otherwise)."""
+    opts = header_enum("GROVER_OPT_")
+    assert opts == {"GROVER_OPT_RESIDENT": 0, "GROVER_OPT_GATE_ENGINE": 1, "GROVER_OPT_WAIT_LIMIT": 2,
+                    "GROVER_OPT_TEST_STALL": 3, "GROVER_OPT_STAGED_PASS": 4}
+    src = open(os.path.join(ROOT, "paper_2005_04635_gb300", "binding.py")).read()
+    for helper, opt in (("set_resident", "GROVER_OPT_RESIDENT"), ("set_gate_engine", "GROVER_OPT_GATE_ENGINE"),
+                        ("set_staged", "GROVER_OPT_STAGED_PASS")):
+        body = src[src.index("def " + helper):]
+        body = body[:body.index("\n    def ", 1)]
+        m = re.search(r"grover_set_option\(self\.handle, (\d+),", body)
+        assert m and int(m.group(1)) == opts[opt], helper
