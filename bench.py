@@ -374,11 +374,29 @@ def run_ours(args):
     return out
 
 
+def tc_pass_supported(n, lo, kb):
+    """The groups the tensor-core pass takes (the others run on CUDA cores)."""
+    if lo == 0:
+        return kb == 7 and n >= 13
+    return 5 <= kb <= 7 and lo >= 13 - kb and lo + kb <= n
+
+
 def gate_groups(n, tensor_cores):
-    """Index-bit group sizes of one H^{(x)n} in grover_iterate_gate: 7-bit groups
-    from bit 0 (tensor cores), else ceil(n / 8) groups of balanced sizes."""
+    """Index-bit group sizes of one H^{(x)n} in grover_iterate_gate: tensor
+    cores take 7 bits from bit 0 and the rest in 7-bit groups, or in near-equal
+    groups where that leaves fewer groups they cannot take; CUDA cores use
+    ceil(n / 8) groups of balanced sizes."""
     if tensor_cores:
-        return [7] * (n // 7) + ([n % 7] if n % 7 else [])
+        greedy = [7] * (n // 7) + ([n % 7] if n % 7 else [])
+        parts = len(greedy) - 1
+        if n < 13 or parts < 1:
+            return greedy
+        rest = n - 7
+        bal = [7] + [rest // parts + (1 if j < rest % parts else 0) for j in range(parts)]
+
+        def fallbacks(gs):
+            return sum(not tc_pass_supported(n, sum(gs[:i]), k) for i, k in enumerate(gs))
+        return bal if fallbacks(bal) < fallbacks(greedy) else greedy
     g = (n + 7) // 8
     return [n // g + (1 if i < n % g else 0) for i in range(g)]
 

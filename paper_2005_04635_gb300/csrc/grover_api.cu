@@ -549,6 +549,27 @@ grover_status grover_iterate_gate(grover_state *s, const grover_marked *mk, uint
         gkb[gi] = kb;
         lo += kb;
     }
+    if (tc) {
+        // 7 bits from bit 0, then the rest in near-equal groups (largest
+        // first) where that leaves fewer groups the tensor-core pass cannot
+        // take than the greedy split's short remainder does
+        auto fallbacks = [&](const int *kbs) {
+            int c = 0;
+            for (int gi = 0, lo = 0; gi < ngroups; lo += kbs[gi], ++gi) c += !tc_pass_supported(s->n, lo, kbs[gi]);
+            return c;
+        };
+        const int rest = s->n - 7, parts = ngroups - 1;
+        if (parts > 0) {
+            int bal[8];
+            bal[0] = 7;
+            for (int j = 0; j < parts; ++j) bal[j + 1] = rest / parts + (j < rest % parts ? 1 : 0);
+            if (fallbacks(bal) < fallbacks(gkb))
+                for (int gi = 0, lo = 0; gi < ngroups; lo += bal[gi], ++gi) {
+                    glo[gi] = lo;
+                    gkb[gi] = bal[gi];
+                }
+        }
+    }
     s->mu_valid = false;
     for (uint64_t t = 0; t < k; ++t) {
         CK(s, launch_oracle(s->amps, s->n, s->dtype, mk->dev, s->stream, s->geo), "oracle launch");

@@ -99,6 +99,11 @@ def test_gate_groups_partition_the_index_bits():
         starts = [sum(cc[:i]) for i in range(len(cc))]
         assert all(s == 0 or s >= 4 for s in starts)
         tc = bench.gate_groups(n, True)
-        assert sum(tc) == n and all(g == 7 for g in tc[:-1]) and 1 <= tc[-1] <= 7
+        assert sum(tc) == n and tc[0] == min(7, n) and all(1 <= g <= 7 for g in tc)
+        assert tc == sorted(tc, reverse=True) and len(tc) == (n + 6) // 7
     assert bench.gate_groups(33, False) == [7, 7, 7, 6, 6]
     assert bench.gate_groups(33, True) == [7, 7, 7, 7, 5]
+    # near-equal tensor-core groups where the greedy split leaves a short remainder
+    assert bench.gate_groups(30, True) == [7, 6, 6, 6, 5]
+    assert bench.gate_groups(18, True) == [7, 6, 5]
+    assert bench.gate_groups(15, True) == [7, 7, 1]  # 7, 4, 4 would leave two CUDA-core groups

@@ -122,7 +122,8 @@ def tc_tol(n, k):
     return k * passes * (K / 16 + 3) * 2.0 ** -24 * K ** 0.5
 
 
-@pytest.mark.parametrize("n,m,k", [(13, 2, 2), (14, 1, 3), (15, 2, 1), (16, 3, 2), (19, 2, 1), (20, 1, 2), (22, 4, 1)])
+@pytest.mark.parametrize("n,m,k", [(13, 2, 2), (14, 1, 3), (15, 2, 1), (16, 3, 2), (18, 2, 1), (19, 2, 1), (20, 1, 2),
+                                   (22, 4, 1), (23, 1, 1)])
 def test_gate_tensor_cores(B, n, m, k):
     marked = inputs.marked_indices(n, m, seed=600 + n)
     psi0 = inputs.gaussian_state(n, seed=601 + n).astype(np.complex64).astype(np.complex128)
