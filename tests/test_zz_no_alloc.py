@@ -2,15 +2,22 @@
 device memory (a framework's allocator owns the memory, or a loop cannot take
 cudaMalloc's device-wide synchronisation): its scratch is a static device
 array instead of a cudaMalloc'd one.  Two calls in a row through the C ABI
-must give what grover_iterate gives on the same input, within the tolerances
-of the other parity tests.  This file is collected last on purpose; it passes
-alone in a fresh process and after the other tests.
+must give what grover_iterate gives on the same input, and what the FP64
+oracle gives from the same stored start, within the tolerances of the other
+parity tests.  This file is collected last on purpose; it passes alone in a
+fresh process and after the other tests.
+
+Oracle bound: an iteration adds an error vector of norm <= 3u (one rounding
+per stored amplitude, norm <= u; the rounding of 2 mu shared by all N
+amplitudes, norm <= sqrt(N) u 2|mu| <= 2u) and is unitary, so after k
+iterations ||gpu - oracle||_2 <= 3 k u (u = 2^-24 complex64, 2^-53 complex128).
 """
 from __future__ import annotations
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_2005_04635_gb300 import inputs
 
 torch = pytest.importorskip("torch")
@@ -50,12 +57,20 @@ def test_noalloc_matches_grover_iterate(dtype, n, m):
     stream = torch.cuda.current_stream().cuda_stream
     code = 0 if dtype == "c64" else 1
     tol = (lambda k: 1e-12) if dtype == "c128" else c64_tol
-    for k, want in ((k1, want1), (k2, want2)):
+    # the oracle from the same stored start (complex64: the FP32-rounded values)
+    start = amps.cpu().numpy().astype(np.complex128)
+    u = 2.0 ** -24 if dtype == "c64" else 2.0 ** -53
+    ora1 = oracle.grover_operator(start.copy(), n, marked, k1)
+    ora2 = oracle.grover_operator(ora1.copy(), n, marked, k2)
+    done = 0
+    for k, want, ora in ((k1, want1, ora1), (k2, want2, ora2)):
         st = lib.grover_iterate_noalloc(amps.data_ptr(), n, code, dmarked.data_ptr(), m, k, stream)
         assert st == 0, lib.grover_last_error(None)
         torch.cuda.synchronize()
+        done += k
         got = amps.cpu().numpy().astype(np.complex128)
         assert np.max(np.abs(got - want)) <= tol(k1 + k2)
+        assert np.linalg.norm(got - ora) <= 3 * done * u + 1e-14
 
 
 def test_noalloc_rejects_bad_sizes():
