@@ -47,11 +47,15 @@ WORKLOADS = {
     "n17-c128-m1": (17, "c128", 1, None, 1711),
     "n20-c64-m1": (20, "c64", 1, None, 2001),
     "n26-c128-m1-k10": (26, "c128", 1, 10, 2631),
+    "n28-c64-m1-k20": (28, "c64", 1, 20, 2801),
+    "n28-c128-m1-k20": (28, "c128", 1, 20, 2811),
 }
 DEFAULT_WORKLOAD = "n33-c64-m1-k100"
 METRIC = "amplitude-updates/s"
 UNIT = "amp-updates/s"
 BYTES_PER_AMP = {"c64": 8, "c128": 16}
+NOMINAL_HBM_GBS = 8000.0      # GB300 HBM3e, nominal (~8 TB/s)
+SMEM_BYTES_PER_CLK = 128      # shared-memory bandwidth of one SM per clock
 
 
 def workload(name):
@@ -200,23 +204,119 @@ def recorded_traffic(w):
     return None
 
 
-# ---- CPU baseline: the FP64 oracle, single thread ------------------------------------------------------
-def cpu_baseline(seconds: float = 12.0, n: int = 26, seed: int = 2601):
-    import oracle
-    from paper_2005_04635_gb300 import inputs
-    marked = inputs.marked_indices(n, 1, seed)
-    psi = oracle.init_uniform(n)
-    t0 = time.perf_counter()
-    oracle.grover_operator(psi, n, marked, 1)
-    t1 = time.perf_counter()
-    iters = max(1, int(seconds / max(t1 - t0, 1e-6)) - 1)
-    t2 = time.perf_counter()
-    oracle.grover_operator(psi, n, marked, iters)
-    t3 = time.perf_counter()
-    value = (1 << n) * (iters + 1) / ((t1 - t0) + (t3 - t2))
-    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"n={n} (2^{n} complex128 amplitudes), M=1, uniform init, {iters + 1} iterations of the FP64 "
-                      f"operator oracle (plain C, one thread), {((t1 - t0) + (t3 - t2)):.1f} s"}
+def hbm_roofline(bytes_per_launch, launch_s, kernel, peaks, peak_src, traffic=None):
+    """Roofline record of an HBM-bound kernel: algorithmic bytes per launch over
+    its average launch time, against the measured copy bandwidth and the
+    nominal HBM bandwidth."""
+    achieved = bytes_per_launch / launch_s / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "peak_nominal": NOMINAL_HBM_GBS,
+            "frac_nominal": achieved / NOMINAL_HBM_GBS, "traffic": traffic, "kernel": kernel,
+            "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": launch_s * 1e3,
+            "peak_source": f"{peak_src} hbm_gbs"}
+
+
+def smem_peak_gbs(sm_count, sm_mhz):
+    """Shared-memory bandwidth of all SMs: 128 bytes per clock per SM."""
+    return sm_count * SMEM_BYTES_PER_CLK * sm_mhz * 1e6 / 1e9
+
+
+def smem_roofline(bytes_per_iter, iter_s, kernel, sm_count, sm_mhz, note):
+    achieved = bytes_per_iter / iter_s / 1e9
+    peak = smem_peak_gbs(sm_count, sm_mhz)
+    return {"bound": "smem", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "kernel": kernel, "algorithmic_bytes_per_launch": None,
+            "algorithmic_bytes_per_iteration": bytes_per_iter, "iteration_us": iter_s * 1e6,
+            "peak_source": f"{sm_count} SMs x {SMEM_BYTES_PER_CLK} B/clock x {sm_mhz:.0f} MHz (sampled SM clock)",
+            "note": note}
+
+
+def p_success_closed_form(n, m, k):
+    """sin^2((2k+1) theta), sin theta = sqrt(M/N): the textbook rotation picture
+    of the Grover iteration for a uniform start."""
+    import math
+    theta = math.asin(math.sqrt(m / (1 << n)))
+    return math.sin((2 * k + 1) * theta) ** 2
+
+
+def resident_kernel(n, dtype):
+    """The on-chip iterator grover_iterate picks (grover.h, GROVER_OPT_RESIDENT)."""
+    return "k_resident_cluster" if n <= (12 if dtype == "c64" else 11) else "k_resident_grid"
+
+
+# ---- CPU baseline: the FP64 oracle on the host cores --------------------------------------------------
+def cpu_model():
+    """The host CPU's model name as lscpu reports it (else the platform string)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+_CPU_WORKER = r"""
+import sys, time, json
+sys.path.insert(0, {root!r})
+import oracle
+from paper_2005_04635_gb300 import inputs
+n, seed, seconds = {n}, {seed}, {seconds}
+marked = inputs.marked_indices(n, 1, seed)
+psi = oracle.init_uniform(n)
+t0 = time.perf_counter()
+oracle.grover_operator(psi, n, marked, 1)
+t1 = time.perf_counter()
+iters = max(1, int(seconds / max(t1 - t0, 1e-6)) - 1)
+t2 = time.perf_counter()
+oracle.grover_operator(psi, n, marked, iters)
+t3 = time.perf_counter()
+print(json.dumps({{"updates": (1 << n) * (iters + 1), "seconds": (t1 - t0) + (t3 - t2)}}), flush=True)
+"""
+
+
+def _oracle_processes(count, n, seconds, seed):
+    """`count` independent processes, each running the plain FP64 oracle on its
+    own seeded instance; returns [(updates, seconds)] per process."""
+    procs = [subprocess.Popen([sys.executable, "-c", _CPU_WORKER.format(root=ROOT, n=n, seed=seed + i,
+                                                                         seconds=seconds)],
+                              stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True) for i in range(count)]
+    res = []
+    for p in procs:
+        out, err = p.communicate(timeout=600)
+        if p.returncode != 0:
+            raise RuntimeError(f"oracle worker failed: {err.strip()[-300:]}")
+        r = json.loads(out.strip().splitlines()[-1])
+        res.append((r["updates"], r["seconds"]))
+    return res
+
+
+def cpu_baseline(seconds: float = 10.0, n: int = 24, seed: int = 2401):
+    """The plain FP64 oracle (operator form, one thread per process) on a bounded
+    sample: one process (the paper's single-thread setup), then one process per
+    host core on independent instances at once (sum of their throughputs).
+    Processes are started fresh (no fork of this CUDA process)."""
+    one = _oracle_processes(1, n, seconds, seed)
+    value1 = one[0][0] / one[0][1]
+    cores = host_cores()
+    many = _oracle_processes(cores, n, seconds, seed + 100)
+    value_all = sum(u / t for u, t in many)
+    return {"value": value1, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"n={n} (2^{n} complex128 amplitudes), M=1, uniform init, {one[0][0] >> n} iterations of the "
+                      f"FP64 operator oracle (plain C, one thread), {one[0][1]:.1f} s",
+            "cpu_model": cpu_model(), "host_cores": cores,
+            "all_cores": {"value": value_all, "unit": UNIT, "cores": cores, "processes": cores,
+                          "sample": f"{cores} processes at once, each the one-thread oracle on its own seeded n={n} "
+                                    f"instance for about {seconds:.0f} s; value = sum of their throughputs"}}
 
 
 # ---- our arm -------------------------------------------------------------------------------------------
@@ -341,37 +441,97 @@ def run_ours(args):
                                 "hbm_gbs": passes * 2 * BYTES_PER_AMP[dtype] * N / gate_s / 1e9,
                                 "operator_speedup": gate_s / pass_s}
 
+    n28 = None
+    if args.n28 and args.workload == DEFAULT_WORKLOAD:
+        n28 = n28_records(binding, inputs, stream)
+
     if rank != 0:
         return None
     # the library's choice of a persistent on-chip iterator (grover.h,
     # GROVER_OPT_RESIDENT: cluster or grid kernel up to n = 22 / 21)
     resident = args.path in ("auto", "resident") and n <= (22 if dtype == "c64" else 21)
     peaks, peak_src = measured_peaks()
-    achieved = BYTES_PER_AMP[dtype] * 2 * N / pass_s / 1e9
-    traffic = recorded_traffic(w)
+    if resident:
+        sm_count = torch.cuda.get_device_properties(0).multi_processor_count
+        sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz") or 2070.0
+        roofline = smem_roofline(
+            2 * BYTES_PER_AMP[dtype] * N, pass_s, resident_kernel(n, dtype), sm_count, sm_mhz,
+            "the state stays in shared memory for all k iterations (one launch); per iteration every amplitude is "
+            "read and written once there; the iteration time is set by the latency of the per-iteration exchange "
+            "of exact partial sums, not by this bandwidth")
+    else:
+        roofline = hbm_roofline(BYTES_PER_AMP[dtype] * 2 * N, pass_s, pass_kernel_name(dtype, N), peaks, peak_src,
+                                recorded_traffic(w))
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if dtype == "c64" else "f64",
         "data": "synthetic (seeded marked indices, uniform initial state)",
         "config": config_of(w, world, args.path),
-        "roofline": None if resident else {
-            "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-            "kernel": pass_kernel_name(dtype, N),
-            "algorithmic_bytes_per_launch": BYTES_PER_AMP[dtype] * 2 * N,
-            "avg_launch_ms": pass_s * 1e3, "peak_source": f"{peak_src} hbm_gbs"},
+        "roofline": roofline,
         "iteration_us": pass_s * 1e6,
         "e2e": {"value": e2e_units / e2e_t, "unit": UNIT, "h2d_bytes_per_step": 8 * M,
                 "d2h_bytes_per_step": 16 * min(M, 16) + 16, "steps": e2e_steps},
         "gpu_launches": args.steps * ((1 if resident else k + 1) + 4),
         "clocks": clk,
-        "result_check": {"p_success": ps, "norm": nrm, "top": [int(x) for x in idx]},
+        "result_check": {"p_success": ps, "p_success_closed_form": p_success_closed_form(n, M, k), "norm": nrm,
+                         "top": [int(x) for x in idx]},
         "gate_path": gate,
     }
+    if n28 is not None:
+        out["n28"] = n28
     if not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline()
+        cb = cpu_baseline()
+        cb["gpu_over_cpu"] = {"one_core": value / cb["value"], "all_cores": value / cb["all_cores"]["value"],
+                              "note": "GPU complex64 value over the FP64 oracle's amplitude-updates/s (complex128)"}
+        out["cpu_baseline"] = cb
     return out
+
+
+# n = 28 half of the metric: full optimal k, one search each, outside the timed
+# region of `value`
+N28_WORKLOADS = ("n28-c64-m1", "n28-c64-m4", "n28-c64-m16", "n28-c128-m1")
+
+
+def n28_records(binding, inputs, stream):
+    """One full search per n = 28 workload (k = floor(pi/4 sqrt(N/M))): the
+    iteration pass's time per launch from CUDA events on the launching stream,
+    its HBM roofline, and P_success against the closed form."""
+    import torch
+    peaks, peak_src = measured_peaks()
+    recs = []
+    for name in N28_WORKLOADS:
+        w = workload(name)
+        n, dtype, M, k = w["n"], w["dtype"], w["M"], w["k"]
+        N = 1 << n
+        marked = inputs.marked_indices(n, M, w["seed"])
+        mk = binding.Marked(n, marked)
+        st = binding.State(n, dtype, stream=stream)
+        st.init_uniform()
+        st.iterate(mk, 3)  # warm-up
+        st.init_uniform()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st.iterate(mk, k)
+        b.record(stream)
+        ps, nrm = st.success_prob(mk)
+        idx, _ = st.measure_topm(min(M, 16))
+        st.sync()
+        it_s = a.elapsed_time(b) / 1e3 / k
+        p_cf = p_success_closed_form(n, M, k)
+        tol = 1e-4 if dtype == "c64" else 1e-11
+        recs.append({
+            "workload": describe(w), "name": name, "n": n, "state_dtype": dtype, "M": M, "k": k, "seed": w["seed"],
+            "iteration_us": it_s * 1e6, "value": N / it_s, "unit": UNIT,
+            "roofline": hbm_roofline(2 * BYTES_PER_AMP[dtype] * N, it_s, pass_kernel_name(dtype, N), peaks, peak_src,
+                                     recorded_traffic(w)),
+            "p_success": ps, "p_success_closed_form": p_cf, "p_success_err": abs(ps - p_cf),
+            "p_success_tolerance": tol, "p_success_ok": abs(ps - p_cf) <= tol,
+            "norm_err": abs(1.0 - nrm), "top_m_is_marked": sorted(int(x) for x in idx) == sorted(int(x) for x in marked)})
+        del st, mk
+        torch.cuda.empty_cache()
+    return recs
 
 
 def tc_pass_supported(n, lo, kb):
@@ -474,6 +634,40 @@ def run_batched(args):
     peaks, peak_src = measured_peaks()
     achieved = hbm * args.steps / t_max / 1e9
     h2d = 4 * len(ns) + 8 * len(ns) + 8 * sum(len(x) for x in marks) + 8 * (len(ns) + 1)
+    # the two classes of instances, each timed alone against its own bound: the
+    # ones the tuned threshold keeps in shared memory (bytes read + written
+    # there per iteration) and the ones streamed through L2 / HBM
+    sm_count = torch.cuda.get_device_properties(0).multi_processor_count
+    sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz") or 2070.0
+    parts = {}
+    for part, sel in (("onchip", [(1 << n) <= onchip_amps for n in ns]),
+                      ("streamed", [(1 << n) > onchip_amps for n in ns])):
+        sub = [i for i, f in enumerate(sel) if f]
+        if not sub:
+            continue
+        sn, sk, sm_ = [ns[i] for i in sub], [ks[i] for i in sub], [marks[i] for i in sub]
+        b3 = binding.Batch(sn, sk, sm_, stream=stream)
+        th3, oc3 = b3.tune()
+        for _ in range(2):
+            b3.run()
+        t3 = _timed_events(b3.run, max(1, min(args.steps, 5)), stream)
+        b3.close()
+        units3 = float(sum((1 << n) * k for n, k in zip(sn, sk)))
+        rec = {"instances": len(sub), "n_range": [min(sn), max(sn)], "ms_per_launch": t3 * 1e3,
+               "value": units3 / t3, "unit": UNIT, "tuned": {"threads": th3, "onchip_vecs": oc3}}
+        if part == "onchip":
+            rec["roofline"] = smem_roofline(
+                16.0 * units3, t3, "k_batch (instances in shared memory)", sm_count, sm_mhz,
+                "one CTA per instance keeps its state in shared memory for all k_i iterations; bytes = 16 per "
+                "amplitude-update (read + write in shared memory); algorithmic_bytes_per_iteration is the whole "
+                "class's per launch")
+            rec["roofline"]["algorithmic_bytes_per_iteration"] = 16.0 * units3
+            rec["roofline"]["iteration_us"] = None
+        else:
+            rec["roofline"] = hbm_roofline(
+                sum(16 * (1 << n) * k + 8 * (1 << n) for n, k in zip(sn, sk)), t3, "k_batch (streamed instances)",
+                peaks, peak_src)
+        parts[part] = rec
     return {
         "metric": METRIC, "value": units_all / t_max, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -484,10 +678,10 @@ def run_batched(args):
                    "tuned": {"threads": threads, "onchip_vecs": onchip},
                    "l2": "per-step traffic 16 B x N x k of the streamed instances (> L2 in total)",
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "k_batch",
-                     "algorithmic_bytes_per_launch": hbm, "peak_source": f"{peak_src} hbm_gbs",
-                     "note": "instances up to the tuned on-chip size run from shared memory and add no HBM bytes"},
+        "roofline": dict(hbm_roofline(hbm, t_max / args.steps, "k_batch", peaks, peak_src),
+                         note="mixed launch: instances up to the tuned on-chip size run from shared memory and add "
+                              "no HBM bytes; the per-class records in `parts` give each class against its own bound"),
+        "parts": parts,
         "e2e": {"value": float(sum((1 << n) * k for n, k in zip(ns, ks))) * e2e_steps / e2e_t, "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8 * len(ns), "steps": e2e_steps},
         "gpu_launches": args.steps, "clocks": clk,
@@ -794,11 +988,17 @@ def run_reference(args):
     value = (1 << n_s) * iters * args.steps / dt
     sample = (f"each step: n={n_s} (2^{n_s} complex128 amplitudes), M={len(marked)}, {iters} iterations of the "
               f"FP64 operator oracle (plain C, one thread), standing in for the {w['name']} workload")
+    cfg = config_of(w, world)
+    cfg["workload"] = (f"bounded sample of the {w['name']} workload: n={n_s} complex128 (FP64 oracle), "
+                       f"M={len(marked)}, uniform init, {iters} iterations per step")
+    cfg["sample"] = {"n": n_s, "state_dtype": "c128", "M": len(marked), "iterations_per_step": iters,
+                     "state_bytes": (1 << n_s) * 16}
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded marked indices, uniform initial state)", "config": config_of(w, world),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "data": "synthetic (seeded marked indices, uniform initial state)", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             "cpu_model": cpu_model(), "host_cores": host_cores()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -826,8 +1026,11 @@ def run_reference_batched(args, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (4096 seeded instances, uniform initial states)",
-            "config": {"workload": "batched: 4096 independent searches, n ~ U[8,20], M ~ U[1,8]", "name": "batched-4096"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "config": {"workload": f"bounded sample of the batched workload (4096 independent searches, n ~ U[8,20], "
+                                   f"M ~ U[1,8]): {len(sample)} instances with n <= 14 per step",
+                       "name": "batched-4096", "sample": {"instances": len(sample), "n_max": 14}},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
+                             "cpu_model": cpu_model(), "host_cores": host_cores()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -839,6 +1042,8 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched-4096"], default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-n28", dest="n28", action="store_false",
+                    help="skip the n = 28 full-search records of the default line")
     ap.add_argument("--study", choices=["precision", "phase", "phase-kernels", "gate-kernels"], default=None,
                     help="run a study instead of the throughput benchmark")
     ap.add_argument("--gate-iters", type=int, default=2,

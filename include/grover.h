@@ -59,7 +59,13 @@ typedef enum { GROVER_C64 = 0, GROVER_C128 = 1 } grover_dtype;
  * Operator"; the paper sums Re and Im separately in one running sum).  Every
  * mode combines per-block partial sums in a fixed order, so a result is
  * bitwise reproducible run to run.
- *   GROVER_ACC_DEFAULT: complex64: GROVER_ACC_FP64; complex128: GROVER_ACC_EXACT.
+ *   GROVER_ACC_DEFAULT: complex64: each thread's 8 amplitudes of a load group
+ *                       summed pairwise in FP32 (exact for equal values), each
+ *                       such group sum added exactly as a fixed-point integer
+ *                       with 100 fractional bits (group sums of magnitude 16
+ *                       or more, Inf and NaN in FP64), threads and blocks
+ *                       combined in integers,
+ *                       one rounding at the end; complex128: GROVER_ACC_EXACT.
  *   GROVER_ACC_FP32:    complex64 only; plain FP32 running sum per thread and an
  *                       FP32 tree across the block, FP64 across blocks.
  *   GROVER_ACC_KAHAN:   complex64 only; Neumaier-compensated FP32 running sum
@@ -349,9 +355,9 @@ grover_status grover_batch_destroy(grover_batch *b);
  *   cuda_stream the stream the work is queued on (asynchronous).
  * Its scratch (per-block partial sums, the mean, a counter) is a file-scope
  * device array of 33,280 bytes, which every GPU that loads the library holds
- * until the process exits; a device that could run more than 2048 blocks of
- * 256 threads at once is rejected with GROVER_EUNSUPPORTED, and n beyond 33
- * (complex64) / 32 (complex128) with GROVER_EINVAL (message in
+ * until the process exits; every pass it launches runs at most 2048 blocks,
+ * one partial-sum slot each, whatever the device could hold at once.  n beyond
+ * 33 (complex64) / 32 (complex128) is rejected with GROVER_EINVAL (message in
  * grover_last_error(NULL)).  The first call on a device looks the array's
  * address up (cudaGetSymbolAddress) with that device current: make that first
  * call before any stream capture.  All calls on a device share the array and

@@ -197,6 +197,7 @@ grover_status grover_create(grover_state **out, int n, grover_dtype dtype, void 
     }
     s->geo.sm_count = sms;
     s->geo.l2_bytes = l2;
+    s->geo.partial_slots = kMaxGrid;
 
     const Layout L = scratch_layout();
     char *base = nullptr;

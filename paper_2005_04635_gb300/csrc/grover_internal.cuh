@@ -55,11 +55,12 @@ struct Scratch {
 };
 constexpr size_t kProbsChunk = size_t(1) << 22;  // 32 MiB of doubles
 
-// Launch geometry derived once per handle.
+// Launch geometry derived once per handle, for the device the handle lives on.
 struct Geometry {
     int sm_count;
     int dev;
     long long l2_bytes;
+    int partial_slots;      // double2 slots of the per-CTA partial-sum array a pass writes into
 };
 
 // Everything a streaming kernel launch needs.

@@ -100,18 +100,16 @@ extern "C" grover_status grover_iterate_noalloc(void *dev_amps, int n, grover_dt
         return noalloc_fail(GROVER_EINVAL, "marked list is not memory of the current device");
 
     Geometry geo;
-    int sms = 0, l2 = 0, threads_per_sm = 0;
+    int sms = 0, l2 = 0;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
-        (e = cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev)) != cudaSuccess ||
-        (e = cudaDeviceGetAttribute(&threads_per_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev)) != cudaSuccess)
+        (e = cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev)) != cudaSuccess)
         return noalloc_fail(GROVER_ECUDA, "cudaDeviceGetAttribute", e);
     geo.sm_count = sms;
     geo.dev = dev;
     geo.l2_bytes = l2;
-    // a pass never runs more CTAs than fit on the device at once
-    const long long max_ctas = (long long)sms * (threads_per_sm / kThreads);
-    if (max_ctas > kNoAllocSlots)
-        return noalloc_fail(GROVER_EUNSUPPORTED, "device holds more resident CTAs than the 2048 partial-sum slots of the static scratch");
+    // the pass launcher caps every grid at the slots of the static array
+    // (one per CTA with FP64 partial sums), whatever the device could hold
+    geo.partial_slots = kNoAllocSlots;
 
     char *base = nullptr;
     if (grover_status st = scratch_address(dev, &base)) return st;

@@ -661,13 +661,19 @@ __global__ void __launch_bounds__(kThreads) k_pass_bulk(PassArgs a) {
         asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // stores complete before the combine
         if (s_bad) {
             // chunk i's wait ran out: report it, and let the loads still in
-            // flight (chunks i .. issued - 1) land, bounded, before the CTA's
-            // shared memory is released
+            // flight (chunks i .. issued - 1) land before the CTA's shared
+            // memory is released.  The pass has failed already, so this wait
+            // gets 64 times the normal bound: a copy that is merely slow lands
+            // here rather than in the shared memory of a later CTA.  The copy
+            // the test hook withheld is never issued and is not waited for.
             if (a.status) atomicExch(a.status, 5);
-            for (uint64_t j = i; j < issued; ++j)
+            const long long drain_limit = a.wait_limit * 64;
+            for (uint64_t j = i; j < issued; ++j) {
+                if (j == 0 && a.stall && blockIdx.x == 0) continue;
                 for (long long polls = 0;
                      !mbar_try_wait(&bar[j % kBulkStages], (unsigned)((j / kBulkStages) & 1));)
-                    if (++polls >= a.wait_limit) break;
+                    if (++polls >= drain_limit) break;
+            }
         }
     }
 
@@ -765,19 +771,32 @@ cudaError_t launch(void (*kernel)(KArgs...), unsigned grid, unsigned block, cuda
     return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
+// Most CTAs a pass may launch: the partial-sum slots it writes (integer modes
+// take three per CTA: two 128-bit integers and the FP64 side sums).
+template <class T, int ACC> int slot_cap(const Geometry &g) {
+    const int per_cta = AccSel<T, ACC>::INT ? 3 : 1;
+    const int c = g.partial_slots / per_cta;
+    return c < kMaxGrid ? c : kMaxGrid;
+}
+
+// CTAs of `kernel` resident on the handle's device at once (queried on every
+// launch: occupancy depends on the device, and a process may drive several).
 template <class K> int resident_ctas(K kernel, const Geometry &g) {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0) != cudaSuccess || per_sm < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0) != cudaSuccess || per_sm < 1) {
+        (void)cudaGetLastError();
         per_sm = 1;
-    long long r = (long long)per_sm * g.sm_count;
+    }
+    const long long r = (long long)per_sm * g.sm_count;
     return (int)(r > kMaxGrid ? kMaxGrid : r);
 }
 
 template <class T, int MARK, int ACC, bool STREAM, bool UPDATE>
 cudaError_t launch_pass_t(const PassArgs &a, cudaStream_t st, const Geometry &g) {
     auto kern = k_pass<T, MARK, ACC, STREAM, UPDATE>;
-    static int cap = 0;
-    if (cap == 0) cap = resident_ctas(kern, g);
+    int cap = resident_ctas(kern, g);
+    const int slots = slot_cap<T, ACC>(g);
+    if (cap > slots) cap = slots;
     const uint64_t tile = (uint64_t)kThreads * kUnroll;
     uint64_t need = (a.nvec + tile - 1) / tile;
     unsigned grid = (unsigned)(need < (uint64_t)cap ? need : (uint64_t)cap);
@@ -793,7 +812,8 @@ cudaError_t launch_bulk_t(const PassArgs &a, cudaStream_t st, const Geometry &g)
     if (e != cudaSuccess) return e;
     const uint64_t nchunks = a.nvec / kBulkChunk, cap = (uint64_t)g.sm_count * kBulkCtasPerSm;
     unsigned grid = (unsigned)(nchunks < cap ? nchunks : cap);
-    if (grid > (unsigned)kMaxGrid) grid = kMaxGrid;
+    const unsigned slots = (unsigned)slot_cap<T, ACC>(g);
+    if (grid > slots) grid = slots;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kThreads);
