@@ -937,15 +937,15 @@ def run_phase_kernels(args):
 
 
 def run_gate_kernels(args):
-    """The conventional circuit on the tensor cores where it is HBM-bound:
-    n=26 complex64 (512 MiB), M=1, uniform start; per-iteration time of
-    grover_iterate_gate (oracle + 8 Walsh-Hadamard passes of 7-, 7-, 7- and
-    5-bit groups, twice) with CUDA events."""
+    """The conventional circuit where it is HBM-bound: n = --gate-n (default
+    26, 512 MiB) complex64, M=1, uniform start; per-iteration time of
+    grover_iterate_gate on each engine (oracle + 2 x the Walsh-Hadamard passes
+    of one H^{(x)n}) with CUDA events, and the passes' GB/s."""
     import torch
     from paper_2005_04635_gb300 import binding, inputs
     torch.cuda.set_device(0)
     binding.lib()
-    n, m, seed = 26, 1, 2601
+    n, m, seed = args.gate_n, 1, 2601
     N = 1 << n
     mk = binding.Marked(n, inputs.marked_indices(n, m, seed))
     stream = torch.cuda.current_stream()
@@ -1046,6 +1046,7 @@ def main(argv=None):
                     help="skip the n = 28 full-search records of the default line")
     ap.add_argument("--study", choices=["precision", "phase", "phase-kernels", "gate-kernels"], default=None,
                     help="run a study instead of the throughput benchmark")
+    ap.add_argument("--gate-n", type=int, default=26, help="qubits of the gate-kernels study")
     ap.add_argument("--gate-iters", type=int, default=2,
                     help="iterations of the conventional circuit timed for comparison (0: skip)")
     ap.add_argument("--path", choices=["auto", "pass", "resident"], default="auto",

@@ -3,35 +3,47 @@
 //
 // A pass applies W (the +-1 Walsh-Hadamard matrix of order K = 2^kb,
 // kb in {5, 6, 7}) to the index bits [lo, lo + kb): for every (outer, inner)
-// position the 2^kb amplitudes along those bits are multiplied by W, i.e. a
-// batched dense contraction.  A CTA tile holds 128 real columns x K mids:
-//   * upper groups (lo >= 7): 64 consecutive amplitudes (re and im = 128
-//     columns) below bit lo, at all K mid values; D = X^T W, so TMEM lane =
-//     column and a warp's stores for one output mid are 128 contiguous bytes;
+// position the K amplitudes along those bits are multiplied by W, i.e. a
+// batched dense contraction (Eq. unitary applied to kb qubits at once).  A
+// tile is 8192 amplitudes = 128 x 128 / K real columns x K mids:
+//   * upper groups (lo >= 13 - kb): 64 * 128 / K consecutive amplitudes below
+//     bit lo (re and im = the columns) at all K mid values; D = X^T W per
+//     block of 128 columns, so TMEM lane = column and a warp's stores for one
+//     output mid are 128 contiguous bytes;
 //   * the lowest group (lo = 0, kb = 7): 64 consecutive blocks of 128
 //     amplitudes (column = (block, re/im)); D = W X, so TMEM lane = output mid
-//     and each thread stores (re, im) pairs, 256 contiguous bytes per warp.
+//     and a warp stores 32 consecutive amplitudes (256 bytes) at once.
 // W is exact in bf16.  Each FP32 amplitude is split into three bf16 slices
-// x = b0 + b1 + b2 (each the round-to-nearest of the remainder).  The b0
-// products accumulate in one FP32 tensor-memory accumulator (A0), the b1 and b2
-// products in a second (A12, about 2^-8 of A0, so the accumulator's own
-// rounding there is below 2^-32 of the result instead of biasing the large
-// one); the epilogue adds A12 + A0 with round to nearest.  Two such pairs
-// (512 TMEM columns) alternate between tiles, so the epilogue of one tile
-// runs while the tensor cores multiply the next.
-// Pipeline per CTA (one per SM): the next tile streams into an fp32 staging
-// buffer by TMA (one tiled cp.async.bulk.tensor copy per tile; the lowest
-// group's with the 128-byte swizzle so its reads are free of bank conflicts;
-// mbarrier transaction count) while the current tile is multiplied and stored.  Operands live in shared memory in
-// the no-swizzle K-major layout (8 x 16-byte core matrices; leading byte
-// offset = 144 B between core matrices along K, stride byte offset = 8-row
-// group stride, both padded against bank conflicts); one thread issues 3 x K/16 tcgen05.mma (M = 128, N = K or
-// 128, K = 16 each) and a tcgen05.commit to an mbarrier; the epilogue reads
-// the accumulators with tcgen05.ld, applies the pass scale (exact power of
-// two) and the phase shift 2|0><0| - I where asked, and stores.  Every
-// mbarrier wait is bounded: on expiry the kernel sets the status word, waits
-// (bounded) for its own copies and MMAs in flight, frees its tensor memory and
-// returns.
+// x = b0 + b1 + b2 (each the round-to-nearest of the remainder; the three hold
+// all 24 bits).  The b0 products accumulate in one FP32 tensor-memory
+// accumulator (A0), the b1 and b2 products in a second (A12, about 2^-8 of
+// A0, so its own rounding is far below the result's); the epilogue adds
+// A12 + A0 with one rounding, scales by an exact power of two and applies the
+// phase shift 2|0><0| - I where asked.
+//
+// Pipeline.  A tile is cut into 8 chunks of 128 columns x 16 mids (one MMA K
+// step each: 8 KiB of FP32, 3 x 4 KiB of bf16).  Warp roles, one CTA per SM:
+//   * TMA warp: one tiled cp.async.bulk.tensor copy per chunk into a ring of
+//     12 FP32 stages (mbarrier transaction counts; the lowest group's copies
+//     with the 128-byte swizzle, so the converters' reads are spread over the
+//     banks);
+//   * 8 converter warps, each owning one slice slot: warp w converts chunks
+//     w, w + 8, ... (eight chunks at once), frees the chunk's stage as soon
+//     as the values are in registers, and writes the slices in the
+//     no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core
+//     matrix, 128 bytes between the two K halves, 256 bytes between 8-row
+//     groups);
+//   * MMA warp: one thread issues the chunk's three tcgen05.mma (kind::f16,
+//     M = 128, N = K or 128, K = 16) and a tcgen05.commit that frees the slot,
+//     and after a tile's last chunk a commit that hands its accumulators on;
+//     two accumulator pairs (512 TMEM columns) alternate between tiles;
+//   * 4 epilogue warps (TMEM lanes 0..127): tcgen05.ld, sum, scale, phase
+//     shift, streaming stores.
+// So the copy of one chunk, the slices of the next and the MMAs and the
+// epilogue of earlier ones all overlap.  Every mbarrier wait is bounded: on
+// expiry the kernel sets the status word, every role leaves its loop, the
+// copies and MMAs already issued are waited for (bounded) and the tensor
+// memory is freed.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -45,85 +57,68 @@
 namespace grv {
 namespace {
 
-constexpr int kTcThreads = 512;
-constexpr int kCols = 128;          // real columns per tile (= MMA M or N)
-constexpr uint32_t kTmemCols = 512; // three accumulators of up to 128 columns
-
+constexpr int kEpiWarps = 4;    // warps 0-3: TMEM lanes 32 w .. 32 w + 31
+constexpr int kTmaWarp = 4;
+constexpr int kMmaWarp = 5;
+constexpr int kConvWarp0 = 6;
+constexpr int kConvWarps = 8;
+constexpr int kTcThreads = 32 * (kConvWarp0 + kConvWarps);  // 448
+constexpr int kSlots = kConvWarps;  // slice slots: converter warp w owns slot w
+// FP32 chunk stages: 96 KiB of copies in flight per SM (as many as shared
+// memory leaves beside the slots and a 7-bit W).  Chunk q uses stage q % 12 and
+// is converted by warp q % 8; successive chunks of a stage belong to different
+// warps, so before it waits for phase q / 12 of full[s] a converter waits until
+// phase q / 12 - 1 of empty[s] has completed (that stage's previous chunk was
+// read).  Both waits are then unambiguous by parity: phase q / 12 - 2 of a
+// stage is chunk q - 24, which this warp itself converted earlier (24 is a
+// multiple of 8).
+constexpr int kRing = 12;
+static_assert((2 * kRing) % kConvWarps == 0, "a stage's phase two back must be the same converter warp's");
+constexpr int kRows = 128;       // real columns per chunk (MMA M, or N for the lowest group)
+constexpr int kChunkK = 16;      // mids per chunk (one MMA K step)
+constexpr int kChunksPerTile = 8;
+constexpr uint32_t kStageBytes = kRows * kChunkK * 4;  // 8 KiB
+constexpr uint32_t kSliceBytes = kRows * kChunkK * 2;  // 4 KiB
+constexpr uint32_t kSlotBytes = 3 * kSliceBytes;
+constexpr uint32_t kTmemCols = 512;                    // 2 tiles x (A0 + A12) x 128 columns
+constexpr uint32_t kLBO = 128, kSBO = 256;             // core-matrix strides along K / along rows
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 // shared-memory matrix descriptor: no swizzle, K-major, descriptor version 1
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((kLBO >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((kSBO >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
 }
 // instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
-// Padded no-swizzle K-major operand layout.  A core matrix (8 rows x 8 bf16
-// along K) is 128 contiguous bytes; core matrices adjacent along K are LBO =
-// 144 bytes apart and 8-row groups SBO bytes apart, SBO = 18 K rounded up to
-// 16 (mod 128).  The 16-byte pads put the eight k-groups of one row, and the
-// rows 4c..4c+3 of eight consecutive c, on distinct bank groups, so the
-// slice stores below are free of shared-memory bank conflicts (unpadded, the
-// k-groups of a row were all 128 bytes apart, on the same banks).
-constexpr uint32_t kLBO = 144;
-__host__ __device__ constexpr uint32_t sbo_of(int K) {
-    return 18u * (uint32_t)K + ((16u - ((18u * (uint32_t)K) & 127u)) & 127u);
-}
-// byte offset of element (row, k) in that layout for a K-column operand
-__device__ __forceinline__ uint32_t kmaj_off(int row, int k, int K) {
-    return (uint32_t)((row >> 3) * sbo_of(K) + (k >> 3) * kLBO + (row & 7) * 16 + (k & 7) * 2);
+// byte offset of (row, k), k < 16, in a [rows][16] bf16 operand chunk
+__device__ __forceinline__ uint32_t core_off(int row, int k) {
+    return (uint32_t)((row >> 3) * kSBO + (k >> 3) * kLBO + (row & 7) * 16 + (k & 7) * 2);
 }
 
-// 128-byte-swizzle K-major operand layout (groups of 6 and 7 bits, K >= 64):
-// a row's 64 elements of one K chunk fill 128 bytes, 8 rows form a 1024-byte
-// atom, and the 16-byte chunk c of row r sits at chunk c ^ (r % 8); the K
-// chunks of an R-row operand follow one another, R / 8 atoms each.  The
-// tensor cores read it at full shared-memory width (the padded layout's
-// 144-byte core-matrix stride straddles 128-byte lines), and stores whose 8
-// rows differ in r % 8, or whose 8 chunks differ, are conflict-free.
-__device__ __forceinline__ uint32_t sw_off(int row, int k, int R) {
-    const int kc = k >> 6, kin = k & 63;
-    return (uint32_t)(kc * (R >> 3) * 1024 + (row >> 3) * 1024 + (row & 7) * 128) +
-           ((uint32_t)((kin >> 3) ^ (row & 7)) << 4) + (uint32_t)(kin & 7) * 2;
-}
-// descriptor of that layout: SBO 1024 B between 8-row atoms, LBO unused (16),
-// layout field 2 (128-byte swizzle); atoms start on 1024-byte boundaries
-__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
-    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
-}
-
-__device__ __forceinline__ void split3(float x, float &b0, float &b1, float &b2) {
-    const __nv_bfloat16 h0 = __float2bfloat16_rn(x);
-    float r = x - __bfloat162float(h0);
-    const __nv_bfloat16 h1 = __float2bfloat16_rn(r);
-    r -= __bfloat162float(h1);
-    b0 = __bfloat162float(h0);
-    b1 = __bfloat162float(h1);
-    b2 = r;  // rounded to bf16 when packed
-}
 __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
     const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<const uint32_t *>(&p);
 }
-// stores 8 consecutive-k values of one column (row) into the three slices at
-// byte offset off (16-byte aligned) of each
-__device__ __forceinline__ void put8(unsigned char *xs, size_t slice_bytes, uint32_t off, const float *v) {
-    float b[3][8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) split3(v[j], b[0][j], b[1][j], b[2][j]);
-#pragma unroll
-    for (int s = 0; s < 3; ++s) {
-        uint4 q;
-        q.x = pack2(b[s][0], b[s][1]);
-        q.y = pack2(b[s][2], b[s][3]);
-        q.z = pack2(b[s][4], b[s][5]);
-        q.w = pack2(b[s][6], b[s][7]);
-        *reinterpret_cast<uint4 *>(xs + s * slice_bytes + off) = q;
-    }
+// Three bf16 slices of two FP32 values x0, x1, packed in pairs (x0 in the low
+// half): s0 = bf16(x), s1 = bf16(x - s0), s2 = bf16(x - s0 - s1), each the
+// round-to-nearest of the remainder (the subtractions are exact, and the last
+// remainder has at most 8 significant bits, so s0 + s1 + s2 = x).
+__device__ __forceinline__ void split3x2(float x0, float x1, uint32_t &s0, uint32_t &s1, uint32_t &s2) {
+    s0 = pack2(x0, x1);
+    const float r0 = x0 - __uint_as_float(s0 << 16), r1 = x1 - __uint_as_float(s0 & 0xFFFF0000u);
+    s1 = pack2(r0, r1);
+    s2 = pack2(r0 - __uint_as_float(s1 << 16), r1 - __uint_as_float(s1 & 0xFFFF0000u));
+}
+// the three slices of 8 values (one 16-byte row of each slice)
+__device__ __forceinline__ void split3x8(const float *x, uint4 &a, uint4 &b, uint4 &c) {
+    split3x2(x[0], x[1], a.x, b.x, c.x);
+    split3x2(x[2], x[3], a.y, b.y, c.y);
+    split3x2(x[4], x[5], a.z, b.z, c.z);
+    split3x2(x[6], x[7], a.w, b.w, c.w);
 }
 
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t *v) {
@@ -134,80 +129,72 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t *v) {
                    "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
                    "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
                  : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
-
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity, long long limit) {
-    uint32_t done = 0;
-    for (long long it = 0; it < limit && !done; ++it) {
-        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                     "selp.u32 %0, 1, 0, p;\n\t}"
-                     : "=r"(done) : "r"(su32(bar)), "r"(parity) : "memory");
-        if (!done) __nanosleep(32);
-    }
+__device__ __forceinline__ bool mbar_try(unsigned long long *bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(done) : "r"(su32(bar)), "r"(parity) : "memory");
     return done != 0;
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
+}
+__device__ __forceinline__ void mma_commit(unsigned long long *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+                 : "memory");
+}
+
+struct TcShared {
+    unsigned long long full[kRing], empty[kRing];    // FP32 stage loaded / read
+    unsigned long long sfull[kSlots], sempty[kSlots];  // slices written / read by the MMAs
+    unsigned long long accfull[2], accempty[2];      // accumulators complete / drained
+    unsigned long long done;                         // every MMA issued has completed
+    uint32_t tslot;
+    volatile int abort;
+};
+
+// Bounded wait on phase `parity` of `bar` by one thread.  Gives up when
+// another role has given up, or after `limit` polls (then it sets the status
+// word and tells the other roles).
+__device__ __forceinline__ bool wait_bar(TcShared &sh, unsigned long long *bar, uint32_t parity, long long limit,
+                                         int *status) {
+    for (long long it = 0; it < limit; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if (sh.abort) return false;
+        __nanosleep(20);
+    }
+    atomicExch(status, 2);
+    sh.abort = 1;
+    return false;
+}
+// The same for a whole warp, with one outcome for all lanes: lane 0 polls;
+// after a completed phase every lane observes it too (so each lane's reads of
+// the data the phase guards are ordered after it; the phase cannot advance
+// before this warp arrives on the barrier that frees it).
+__device__ __forceinline__ bool warp_wait(TcShared &sh, unsigned long long *bar, uint32_t parity, long long limit,
+                                          int *status) {
+    int ok = 0;
+    if ((threadIdx.x & 31) == 0) ok = wait_bar(sh, bar, parity, limit, status) ? 1 : 0;
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (ok) (void)mbar_try(bar, parity);
+    return ok != 0;
 }
 
 // Real columns of a tile: 128 for the lowest group (64 blocks x re/im); for an
-// upper group 128 x 128 / K, so every tile holds 8192 amplitudes (64 KiB) and
-// a K < 128 pass runs 128 / K column blocks of 128 through the MMAs.
-template <int KB, bool LOW> __host__ __device__ constexpr int tile_cols() { return LOW ? kCols : kCols * (128 >> KB); }
-// box width (floats) of one tensor copy of an upper-group tile (at most 256)
-template <int KB> __host__ __device__ constexpr int box_cols() {
-    return tile_cols<KB, false>() < 256 ? tile_cols<KB, false>() : 256;
-}
+// upper group 128 x 128 / K, run as 128 / K blocks of 128 columns.
+template <int KB, bool LOW> __host__ __device__ constexpr int tile_cols() { return LOW ? kRows : kRows * (128 >> KB); }
 
-// Tile geometry: first amplitude of the tile (the mids are 2^lo apart).
+// First amplitude of a tile (the mids are 2^lo apart).
 template <int KB, bool LOW> __device__ __forceinline__ uint64_t tile_base(uint64_t tile, int lo) {
-    constexpr int K = 1 << KB;
-    if (LOW) return tile * (uint64_t)(kCols / 2) * K;  // 64 blocks of K amplitudes
+    if (LOW) return tile * 8192ull;
     constexpr int AMPS = tile_cols<KB, false>() / 2;
-    const uint64_t chunks = (1ull << lo) / AMPS;
-    return ((tile / chunks) << (lo + KB)) | ((tile % chunks) * AMPS);
-}
-
-// Warp 0 streams one tile of fp32 amplitudes into the staging buffer: the
-// lowest group is one contiguous block, an upper group K rows of 512 bytes.
-template <int KB, bool LOW>
-__device__ __forceinline__ void issue_tile_load(const float *amps, const CUtensorMap *tmap, uint64_t tile, int lo,
-                                                unsigned char *stage, unsigned long long *bar, int lane) {
-    constexpr int K = 1 << KB;
-    constexpr uint32_t TILEB = (uint32_t)K * tile_cols<KB, LOW>() * 4;  // 64 KiB
-    const uint64_t abase = tile_base<KB, LOW>(tile, lo);
-    if (lane == 0)
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(TILEB) : "memory");
-    __syncwarp();
-    if (LOW) {
-        // one tiled copy with the 128-byte swizzle: box {32 floats, 8 lines,
-        // 64 blocks} of the view [block][8 lines][32 floats]; x = 0, y = 0,
-        // z = first block of the tile
-        if (lane == 0) {
-            const int z = (int)(abase / K);
-            asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-                         "[%0], [%1, {%2, %3, %4}], [%5];"
-                         ::"r"(su32(stage)), "l"(tmap), "r"(0), "r"(0), "r"(z), "r"(su32(bar)) : "memory");
-        }
-    } else if (lane == 0) {
-        // tiled copies of box {BOX floats, K mids, 1 outer} of the view
-        // [outer][mid][2^(lo+1) floats]; x = chunk * COLS + b * BOX floats (a
-        // multiple of 16 bytes), y = 0, z = outer; copy b lands as its own
-        // [K][BOX] block of the stage
-        constexpr int COLS = tile_cols<KB, false>(), BOX = box_cols<KB>();
-        const uint64_t chunks = (1ull << lo) / (COLS / 2);
-        const int z = (int)(tile / chunks);
-#pragma unroll
-        for (int b = 0; b < COLS / BOX; ++b) {
-            const int x = (int)((tile % chunks) * COLS) + b * BOX;
-            asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-                         "[%0], [%1, {%2, %3, %4}], [%5];"
-                         ::"r"(su32(stage + (size_t)b * K * BOX * 4)), "l"(tmap), "r"(x), "r"(0), "r"(z),
-                           "r"(su32(bar)) : "memory");
-        }
-    }
-    (void)amps;
+    const uint64_t per_outer = (1ull << lo) / AMPS;
+    return ((tile / per_outer) << (lo + KB)) | ((tile % per_outer) * AMPS);
 }
 
 template <int KB, bool LOW>
@@ -215,284 +202,308 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 k_wht_tc(float *amps, const __grid_constant__ CUtensorMap tmap, int lo, uint64_t ntiles, float scale,
          int negate_but_zero, int *status, long long wait_limit, int stall) {
     constexpr int K = 1 << KB;
-    constexpr int COLS = tile_cols<KB, LOW>();            // real columns (operand rows)
-    constexpr int NB = COLS / kCols;                        // column blocks of 128 (MMA M)
-    constexpr bool SW = KB >= 6;                            // 128-byte-swizzle operands
-    constexpr size_t STAGE = (size_t)K * COLS * 4;          // fp32 tile, 64 KiB
-    constexpr uint32_t SBO = sbo_of(K);
-    constexpr uint32_t LBO = kLBO;
-    constexpr size_t SLICE = SW ? (size_t)COLS * K * 2 : (size_t)(COLS / 8) * SBO;  // one bf16 slice of the tile
-    constexpr int M_MMA = 128;
-    constexpr int N_MMA = LOW ? kCols : K;                  // accumulator columns; A12 sits N_MMA after A0
+    constexpr int KC = K / kChunkK;          // chunks per block of 128 columns
+    constexpr int NB = kChunksPerTile / KC;  // blocks of 128 columns per tile
+    constexpr int N_MMA = LOW ? kRows : K;   // accumulator columns per block
+    constexpr int RING = kRing;
     static_assert(!LOW || KB == 7, "the lowest group uses W as the 128-row operand");
+    static_assert(NB * 2 * N_MMA == 256, "one tile's accumulators fill 256 TMEM columns");
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char *stage = smem;                        // fp32 tile from global
-    unsigned char *xs = smem + STAGE;                   // [3][SLICE] bf16 slices
-    unsigned char *ws = smem + STAGE + 3 * SLICE;       // W, K x K bf16
-    __shared__ __align__(8) unsigned long long tma_bar, mma_bar;
-    __shared__ uint32_t tslot;
-    __shared__ int s_abort;
+    unsigned char *ring = smem;                                 // [RING][8 KiB] FP32 chunks
+    unsigned char *slots = smem + RING * kStageBytes;           // [kSlots][3][4 KiB] bf16 slices
+    unsigned char *wsm = slots + kSlots * kSlotBytes;           // [KC][K rows][16] bf16 W
+    TcShared &sh = *reinterpret_cast<TcShared *>(wsm + K * K * 2);  // barriers (all shared memory is dynamic)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // the 128-byte swizzle of the staged tile repeats every 1024 bytes: the
-    // stage must start on such a boundary (the reads undo the pattern from
-    // offsets relative to it)
-    if (su32(stage) & 1023u) {
+    // the 128-byte swizzle of the lowest group's stages repeats every 1024
+    // bytes: the ring must start on such a boundary
+    if (su32(ring) & 1023u) {
         if (tid == 0) atomicExch(status, 4);
         return;
     }
-    for (int i = tid; i < K * K / 8; i += kTcThreads) {  // W[n][k] = (-1)^popcount(n & k)
+    // W[n][k] = w (-1)^popcount(n & k), w = the pass scale (a power of two),
+    // negated when the pass applies the phase shift 2|0><0| - I (every
+    // amplitude but index 0 negated; the epilogue restores index 0): exact in
+    // bf16, so the products and sums are those of the unscaled pass scaled
+    const float wv = negate_but_zero ? -scale : scale;
+    for (int i = tid; i < K * K / 8; i += kTcThreads) {
         const int n = i / (K / 8), k0 = (i % (K / 8)) * 8;
         float v[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] = (__popc(n & (k0 + j)) & 1) ? -1.0f : 1.0f;
+        for (int j = 0; j < 8; ++j) v[j] = (__popc(n & (k0 + j)) & 1) ? -wv : wv;
         uint4 q;
         q.x = pack2(v[0], v[1]);
         q.y = pack2(v[2], v[3]);
         q.z = pack2(v[4], v[5]);
         q.w = pack2(v[6], v[7]);
-        *reinterpret_cast<uint4 *>(ws + (SW ? sw_off(n, k0, K) : kmaj_off(n, k0, K))) = q;
+        *reinterpret_cast<uint4 *>(wsm + (k0 >> 4) * (K * 32) + core_off(n, k0 & 15)) = q;
     }
     if (tid == 0) {
-        s_abort = 0;
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&tma_bar)) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&mma_bar)) : "memory");
+        sh.abort = 0;
+        for (int s = 0; s < RING; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&sh.full[s])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&sh.empty[s])) : "memory");
+        }
+        for (int s = 0; s < kSlots; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&sh.sfull[s])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&sh.sempty[s])) : "memory");
+        }
+        for (int b = 0; b < 2; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&sh.accfull[b])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&sh.accempty[b])), "r"(kEpiWarps) : "memory");
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&sh.done)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tslot)),
+    if (warp == kMmaWarp) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&sh.tslot)),
                      "r"(kTmemCols) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // W, for the tensor cores
     fence_before();
     __syncthreads();
     fence_after();
-    const uint32_t taddr = tslot;
-    // loads_done / mmas_done count completed phases of the two mbarriers; the
-    // parity of the next phase to wait for is the count's low bit
-    uint32_t loads_done = 0, mmas_done = 0;
-    bool load_pending = blockIdx.x < ntiles, mma_pending = false;
-    if (warp == 0 && load_pending) issue_tile_load<KB, LOW>(amps, &tmap, blockIdx.x, lo, stage, &tma_bar, lane);
+    const uint32_t taddr = sh.tslot;
 
-    // Epilogue of a finished tile from TMEM buffer `buf`: A12 + A0 (one
-    // rounding), scale, phase shift, store.
-    auto epilogue = [&](uint64_t etile, uint32_t buf) {
-        const uint64_t abase = tile_base<KB, LOW>(etile, lo);
-        const int lg = warp & 3, cw = warp >> 2;
-        constexpr int CPB = N_MMA / 32;  // 32-column chunks per column block
-        if (cw < NB * CPB) {
-            const int blk = cw / CPB, cg = cw % CPB;
-            uint32_t a[32], b[32];
-            const uint32_t t0 = taddr + 256u * buf + ((uint32_t)(32 * lg) << 16) + (uint32_t)(blk * 2 * N_MMA + 32 * cg);
-            tmem_ld32(t0 + (uint32_t)N_MMA, a);
-            tmem_ld32(t0, b);
-#pragma unroll
-            for (int j = 0; j < 32; ++j) a[j] = __float_as_uint(__uint_as_float(a[j]) + __uint_as_float(b[j]));
-            const int row = 32 * lg + lane;
-            if (LOW) {
-                // row = output mid, registers = 16 blocks x (re, im); lanes 2l and
-                // 2l + 1 hold mids r and r + 1: the even lane stores both for the
-                // even blocks, the odd lane for the odd blocks (16-byte stores)
-                const bool odd = lane & 1;
-                const int r0 = row & ~1;
-#pragma unroll
-                for (int p = 0; p < 8; ++p) {
-                    const float e0 = __uint_as_float(a[4 * p]), e1 = __uint_as_float(a[4 * p + 1]);
-                    const float o0 = __uint_as_float(a[4 * p + 2]), o1 = __uint_as_float(a[4 * p + 3]);
-                    // even lane gives its odd-block pair, odd lane its even-block pair
-                    const float g0 = __shfl_xor_sync(0xffffffffu, odd ? e0 : o0, 1);
-                    const float g1 = __shfl_xor_sync(0xffffffffu, odd ? e1 : o1, 1);
-                    // (mid r0: re, im), (mid r0 + 1: re, im) of block 2p + odd
-                    float4 v = odd ? make_float4(g0, g1, o0, o1) : make_float4(e0, e1, g0, g1);
-                    const uint64_t a0 = abase + (uint64_t)(16 * cg + 2 * p + (odd ? 1 : 0)) * K + r0;
-                    v.x *= scale;
-                    v.y *= scale;
-                    v.z *= scale;
-                    v.w *= scale;
-                    if (negate_but_zero) {
-                        if (a0 != 0) {
-                            v.x = -v.x;
-                            v.y = -v.y;
-                        }
-                        v.z = -v.z;
-                        v.w = -v.w;
-                    }
-                    __stcs(reinterpret_cast<float4 *>(amps) + a0 / 2, v);
-                }
-            } else {
-                // row = column (re or im of amplitude col / 2), registers = output
-                // mids; lanes 2l and 2l + 1 hold re and im of one amplitude: they
-                // swap halves so each stores (re, im) pairs for 16 mids
-                const int col = kCols * blk + row;
-                const uint64_t ar = abase + (uint64_t)(col >> 1);
-                const bool odd = lane & 1;
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    // even lane keeps mid 2j (its re) and receives the im of mid 2j;
-                    // odd lane keeps mid 2j + 1 (its im) and receives the re of mid 2j + 1
-                    const float mine_e = __uint_as_float(a[2 * j]), mine_o = __uint_as_float(a[2 * j + 1]);
-                    const float give = odd ? mine_e : mine_o;
-                    const float got = __shfl_xor_sync(0xffffffffu, give, 1);
-                    const int mid = 32 * cg + 2 * j + (odd ? 1 : 0);
-                    const uint64_t a0 = ar + ((uint64_t)mid << lo);
-                    float re = (odd ? got : mine_e) * scale, im = (odd ? mine_o : got) * scale;
-                    if (negate_but_zero && a0 != 0) {
-                        re = -re;
-                        im = -im;
-                    }
-                    __stcs(reinterpret_cast<float2 *>(amps) + a0, make_float2(re, im));
-                }
-            }
-        }
-    };
+    // this CTA's tiles: blockIdx.x, blockIdx.x + gridDim.x, ...
+    const uint64_t my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const uint64_t my_chunks = my_tiles * kChunksPerTile;
 
-    // Per tile i: build the slices of tile i; issue the load of tile i + 1 and
-    // the MMAs of tile i into TMEM buffer i & 1; while they run, the epilogue
-    // of tile i - 1 drains buffer (i - 1) & 1; then wait for the MMAs (the
-    // slices are free again).
-    uint64_t prev = ~0ull;
-    uint32_t it = 0;
-    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-        // ---- staged fp32 tile -> three bf16 slices ----
-        if (!mbar_wait(&tma_bar, loads_done & 1, wait_limit)) {
-            atomicExch(status, 2);
-            s_abort = 1;
-        }
-        __syncthreads();
-        if (s_abort) break;
-        ++loads_done;
-        load_pending = false;
-        if (LOW) {
-            // unit = (block o, k-group of 8 mids): 8 complex = 4 float4 contiguous
-            // the stage holds 128-byte lines whose 16-byte chunks the copy
-            // permuted: chunk c of line L sits at chunk c ^ (L & 7); the eight
-            // threads of a load phase then read eight different bank groups
-            for (int u = tid; u < (kCols / 2) * (K / 8); u += kTcThreads) {
-                const int kg = u % (K / 8), o = u / (K / 8);
-                float re[8], im[8];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const uint32_t logical = (uint32_t)o * (K * 8) + (uint32_t)kg * 64 + (uint32_t)q * 16;
-                    const uint32_t phys = logical ^ (((logical >> 7) & 7u) << 4);
-                    const float4 c = *reinterpret_cast<const float4 *>(stage + phys);
-                    re[2 * q] = c.x;
-                    im[2 * q] = c.y;
-                    re[2 * q + 1] = c.z;
-                    im[2 * q + 1] = c.w;
+    if (warp == kTmaWarp) {
+        // ---- producer: one tensor copy per chunk -------------------------------------
+        uint64_t issued = 0;
+        if (lane == 0) {
+            for (uint64_t q = 0; q < my_chunks; ++q) {
+                const int s = (int)(q % RING);
+                if (q >= (uint64_t)RING &&
+                    !wait_bar(sh, &sh.empty[s], (uint32_t)((q / RING - 1) & 1), wait_limit, status))
+                    break;
+                const uint64_t tile = blockIdx.x + (q / kChunksPerTile) * gridDim.x;
+                const int j = (int)(q % kChunksPerTile), blk = j / KC, c = j % KC;
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(&sh.full[s])),
+                             "r"(kStageBytes) : "memory");
+                if (LOW) {
+                    // view [block of 128 amplitudes][256 floats], box {32 floats, 64 blocks}
+                    const int x = 32 * c, y = (int)(tile * 64);
+                    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+                                 "[%0], [%1, {%2, %3}], [%4];"
+                                 ::"r"(su32(ring + s * kStageBytes)), "l"(&tmap), "r"(x), "r"(y), "r"(su32(&sh.full[s]))
+                                 : "memory");
+                } else {
+                    // view [outer][K mids][2^(lo+1) floats], box {128 floats, 16 mids, 1}
+                    constexpr int COLS = tile_cols<KB, false>();
+                    const uint64_t per_outer = (1ull << (lo + 1)) / COLS;
+                    const int x = (int)((tile % per_outer) * COLS) + blk * kRows, y = kChunkK * c;
+                    const int z = (int)(tile / per_outer);
+                    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+                                 "[%0], [%1, {%2, %3, %4}], [%5];"
+                                 ::"r"(su32(ring + s * kStageBytes)), "l"(&tmap), "r"(x), "r"(y), "r"(z),
+                                   "r"(su32(&sh.full[s]))
+                                 : "memory");
                 }
-                put8(xs, SLICE, SW ? sw_off(2 * o, kg * 8, COLS) : kmaj_off(2 * o, kg * 8, K), re);
-                put8(xs, SLICE, SW ? sw_off(2 * o + 1, kg * 8, COLS) : kmaj_off(2 * o + 1, kg * 8, K), im);
+                ++issued;
             }
-        } else {
-            // copy b of the tile holds columns [b BOX, (b + 1) BOX) as a [K][BOX] block
-            constexpr int BOX = box_cols<KB>();
-            if constexpr (SW) {
-                // unit = (k-group of 8 mids, column): consecutive threads read
-                // consecutive columns of each mid row and store rows whose r % 8
-                // differ (both conflict-free)
-                const float *stf = reinterpret_cast<const float *>(stage);
-                for (int u = tid; u < (K / 8) * COLS; u += kTcThreads) {
-                    const int c = u % COLS, kg = u / COLS;
-                    const float *src = stf + (size_t)(c / BOX) * K * BOX + (size_t)(kg * 8) * BOX + (c % BOX);
-                    float col[8];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) col[j] = src[(size_t)j * BOX];
-                    put8(xs, SLICE, sw_off(c, kg * 8, COLS), col);
-                }
-            } else
-            // unit = (k-group of 8 mids, float4 column group)
-            for (int u = tid; u < (K / 8) * (COLS / 4); u += kTcThreads) {
-                const int c4 = u % (COLS / 4), kg = u / (COLS / 4);
-                const int bx = (4 * c4) / BOX, w4 = ((4 * c4) % BOX) / 4;
-                const float4 *blk4 = reinterpret_cast<const float4 *>(stage) + (size_t)bx * K * (BOX / 4);
-                float col[4][8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const float4 c = blk4[(size_t)(kg * 8 + j) * (BOX / 4) + w4];
-                    col[0][j] = c.x;
-                    col[1][j] = c.y;
-                    col[2][j] = c.z;
-                    col[3][j] = c.w;
-                }
-#pragma unroll
-                for (int q = 0; q < 4; ++q) put8(xs, SLICE, kmaj_off(4 * c4 + q, kg * 8, K), col[q]);
+            // every copy issued must have landed before the CTA's shared memory
+            // is released (after an abort some may still be in flight); the
+            // kernel has failed by then, so the wait may be long
+            const uint64_t first = issued > (uint64_t)RING ? issued - RING : 0;
+            for (uint64_t q = first; q < issued; ++q) {
+                const int s = (int)(q % RING);
+                for (long long it = 0; it < 64 * wait_limit && !mbar_try(&sh.full[s], (uint32_t)((q / RING) & 1)); ++it)
+                    __nanosleep(20);
             }
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        fence_before();
-        __syncthreads();
-        fence_after();
-        // ---- next tile's load ----
-        const uint64_t next = tile + gridDim.x;
-        if (warp == 0 && next < ntiles) issue_tile_load<KB, LOW>(amps, &tmap, next, lo, stage, &tma_bar, lane);
-        load_pending = next < ntiles;
-        // ---- MMA into buffer it & 1: A0 = W b0 (or b0 W), A12 = W (b1 + b2) ----
-        if (tid == 0) {
-            constexpr uint32_t idesc = idesc_bf16(M_MMA, N_MMA);
-            const uint32_t tb = taddr + 256u * (it & 1u);
-#pragma unroll 1
-            for (int blk = 0; blk < NB; ++blk) {
-#pragma unroll 1
-                for (int s = 0; s < 3; ++s) {
-#pragma unroll 1
-                    for (int kk = 0; kk < K / 16; ++kk) {
-                        // column block blk: operand rows [128 blk, 128 blk + 128)
-                        uint64_t dx, dw;
-                        if constexpr (SW) {
-                            const uint32_t kin = (uint32_t)(kk & 3) * 32u, kc = (uint32_t)(kk >> 2);
-                            dx = smem_desc_sw128(su32(xs + s * SLICE) + kc * (COLS / 8) * 1024u + (uint32_t)blk * 16u * 1024u +
-                                                 kin);
-                            dw = smem_desc_sw128(su32(ws) + kc * (K / 8) * 1024u + kin);
-                        } else {
-                            dx = smem_desc(su32(xs + s * SLICE) + (uint32_t)blk * 16u * SBO + kk * 2 * LBO, LBO, SBO);
-                            dw = smem_desc(su32(ws) + kk * 2 * LBO, LBO, SBO);
-                        }
-                        const uint64_t da = LOW ? dw : dx;
-                        const uint64_t db = LOW ? dx : dw;
-                        const uint32_t acc = (s == 2) || kk != 0;
+    } else if (warp == kMmaWarp) {
+        // ---- MMA issue: one thread --------------------------------------------------
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(128, N_MMA);
+            uint64_t q = 0;
+            bool ok = true;
+            for (uint64_t i = 0; ok && i < my_tiles; ++i) {
+                const uint32_t b = (uint32_t)(i & 1);
+                if (i >= 2 && !wait_bar(sh, &sh.accempty[b], (uint32_t)((i / 2 - 1) & 1), wait_limit, status)) break;
+                fence_after();
+                for (int j = 0; j < kChunksPerTile; ++j, ++q) {
+                    const int p = (int)(q % kSlots), blk = j / KC, c = j % KC;
+                    if (!wait_bar(sh, &sh.sfull[p], (uint32_t)((q / kSlots) & 1), wait_limit, status)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    const uint32_t d0 = taddr + 256u * b + (uint32_t)(blk * 2 * N_MMA);
+                    const uint64_t dw = smem_desc(su32(wsm + c * (K * 32)));
+#pragma unroll
+                    for (int sl = 0; sl < 3; ++sl) {
+                        const uint64_t dx = smem_desc(su32(slots + p * kSlotBytes + sl * kSliceBytes));
+                        const uint64_t da = LOW ? dw : dx, db = LOW ? dx : dw;
+                        const uint32_t d = d0 + (sl ? (uint32_t)N_MMA : 0u);
+                        const uint32_t acc = (sl == 2 || c != 0) ? 1u : 0u;
                         asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                                      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-                                     ::"r"(tb + (uint32_t)(blk * 2 * N_MMA) + (s ? (uint32_t)N_MMA : 0u)), "l"(da),
-                                       "l"(db), "r"(idesc), "r"(acc) : "memory");
+                                     ::"r"(d), "l"(da), "l"(db), "r"(idesc), "r"(acc) : "memory");
+                    }
+                    mma_commit(&sh.sempty[p]);  // the slot is free once these MMAs have read it
+                }
+                if (!ok) break;
+                // test hook: without this commit the epilogue's wait runs out
+                if (!(stall && i == 0)) mma_commit(&sh.accfull[b]);
+            }
+            // every MMA issued has completed before the tensor memory is freed
+            mma_commit(&sh.done);
+            for (long long it = 0; it < 64 * wait_limit && !mbar_try(&sh.done, 0u); ++it) __nanosleep(20);
+        }
+    } else if (warp >= kConvWarp0) {
+        // ---- converters: FP32 chunk -> three bf16 slices ---------------------------------
+        // warp w converts chunks w, w + 8, ... from stage w into slot w, so eight
+        // chunks are converted at once; lane l takes the columns l, l + 32,
+        // l + 64, l + 96 (all 16 mids of each) and writes 16-byte rows, the 32
+        // lanes of a store covering four whole 128-byte core-matrix rows
+        const int w = warp - kConvWarp0;
+        for (uint64_t q = (uint64_t)w; q < my_chunks; q += kConvWarps) {
+            const uint32_t use = (uint32_t)(q / kConvWarps);  // uses of slot w so far
+            const int s = (int)(q % RING);
+            const uint32_t ph = (uint32_t)(q / RING);
+            if (ph >= 1 && !warp_wait(sh, &sh.empty[s], (ph - 1) & 1u, wait_limit, status)) break;
+            if (!warp_wait(sh, &sh.full[s], ph & 1u, wait_limit, status)) break;
+            const unsigned char *st = ring + s * kStageBytes;
+            unsigned char *slot = slots + w * kSlotBytes;
+            if (LOW) {
+                // unit u = lane + 32 r: block u / 2 (columns 2b = re, 2b + 1 = im),
+                // mids 8 (u & 1) .. + 7, read as four 16-byte (re, im, re, im)
+                // pieces; the stage holds 128-byte lines (one per block) whose
+                // 16-byte chunks the copy permuted, chunk c of line L at
+                // c ^ (L & 7), so the eight lanes of a load phase hit eight
+                // different chunks
+                float4 v[4][4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const int u = lane + 32 * r, b = u >> 1, h = u & 1;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        v[r][c] = *reinterpret_cast<const float4 *>(st + b * 128 +
+                                                                    ((uint32_t)((4 * h + c) ^ (b & 7)) << 4));
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sh.empty[s]);  // the stage is read
+                if (use >= 1 && !warp_wait(sh, &sh.sempty[w], (use - 1) & 1u, wait_limit, status)) break;
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const int u = lane + 32 * r, b = u >> 1, h = u & 1;
+                    float re[8], im[8];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        re[2 * c] = v[r][c].x;
+                        im[2 * c] = v[r][c].y;
+                        re[2 * c + 1] = v[r][c].z;
+                        im[2 * c + 1] = v[r][c].w;
+                    }
+                    uint4 a0, a1, a2;
+                    split3x8(re, a0, a1, a2);
+                    *reinterpret_cast<uint4 *>(slot + core_off(2 * b, 8 * h)) = a0;
+                    *reinterpret_cast<uint4 *>(slot + kSliceBytes + core_off(2 * b, 8 * h)) = a1;
+                    *reinterpret_cast<uint4 *>(slot + 2 * kSliceBytes + core_off(2 * b, 8 * h)) = a2;
+                    split3x8(im, a0, a1, a2);
+                    *reinterpret_cast<uint4 *>(slot + core_off(2 * b + 1, 8 * h)) = a0;
+                    *reinterpret_cast<uint4 *>(slot + kSliceBytes + core_off(2 * b + 1, 8 * h)) = a1;
+                    *reinterpret_cast<uint4 *>(slot + 2 * kSliceBytes + core_off(2 * b + 1, 8 * h)) = a2;
+                }
+            } else {
+                // [16 mids][128 floats]; lane l takes columns l, l + 32, l + 64,
+                // l + 96 (consecutive lanes: consecutive floats, whole 128-byte
+                // rows of the core matrices on the stores)
+                float v[4][16];
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int mid = 0; mid < 16; ++mid)
+                        v[r][mid] = reinterpret_cast<const float *>(st)[mid * kRows + lane + 32 * r];
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sh.empty[s]);  // the stage is read
+                if (use >= 1 && !warp_wait(sh, &sh.sempty[w], (use - 1) & 1u, wait_limit, status)) break;
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        uint4 a0, a1, a2;
+                        split3x8(&v[r][8 * h], a0, a1, a2);
+                        const uint32_t off = core_off(lane + 32 * r, 8 * h);
+                        *reinterpret_cast<uint4 *>(slot + off) = a0;
+                        *reinterpret_cast<uint4 *>(slot + kSliceBytes + off) = a1;
+                        *reinterpret_cast<uint4 *>(slot + 2 * kSliceBytes + off) = a2;
+                    }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // slices, for the tensor cores
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sh.sfull[w]);
+        }
+    } else {
+        // ---- epilogue: warps 0-3, TMEM lanes 32 warp .. 32 warp + 31 ------------------------
+        const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+        for (uint64_t i = 0; i < my_tiles; ++i) {
+            const uint32_t b = (uint32_t)(i & 1);
+            if (!warp_wait(sh, &sh.accfull[b], (uint32_t)((i / 2) & 1), wait_limit, status)) break;
+            fence_after();
+            const uint64_t tile = blockIdx.x + i * gridDim.x;
+            const uint64_t abase = tile_base<KB, LOW>(tile, lo);
+            constexpr int GROUPS = NB * (N_MMA / 32);  // 32-column groups per accumulator
+#pragma unroll 1
+            for (int g = 0; g < GROUPS; ++g) {
+                const int blk = g / (N_MMA / 32), cg = g % (N_MMA / 32);
+                uint32_t a[32], z[32];
+                const uint32_t t0 = taddr + lane_base + 256u * b + (uint32_t)(blk * 2 * N_MMA + 32 * cg);
+                tmem_ld32(t0 + (uint32_t)N_MMA, a);  // A12
+                tmem_ld32(t0, z);                    // A0
+                tmem_wait_ld();
+                if (g == GROUPS - 1) {
+                    // the accumulators of this tile are read: hand them back
+                    fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&sh.accempty[b]);
+                }
+                // W carried the scale and the phase-shift sign; only amplitude 0
+                // (in tile 0, first group, warp 0) must not be negated
+                const bool fix0 = negate_but_zero && tile == 0 && g == 0 && warp == 0;
+                if (LOW) {
+                    // lane = output mid r; registers = 16 blocks x (re, im):
+                    // stores of 32 consecutive amplitudes per warp
+                    const int r = 32 * warp + lane;
+                    float2 *p = reinterpret_cast<float2 *>(amps) + abase + (uint64_t)(16 * cg) * 128 + r;
+#pragma unroll
+                    for (int t = 0; t < 16; ++t) {
+                        float re = __uint_as_float(a[2 * t]) + __uint_as_float(z[2 * t]);
+                        float im = __uint_as_float(a[2 * t + 1]) + __uint_as_float(z[2 * t + 1]);
+                        if (t == 0 && fix0 && lane == 0) {
+                            re = -re;
+                            im = -im;
+                        }
+                        __stcs(p + t * 128, make_float2(re, im));
+                    }
+                } else {
+                    // lane = column (re or im of amplitude col / 2), registers =
+                    // 32 consecutive output mids: each store writes 32
+                    // consecutive floats of one mid
+                    const int col = kRows * blk + 32 * warp + lane;
+                    float *p = amps + 2 * abase + col + ((uint64_t)(32 * cg) << (lo + 1));
+                    const uint64_t stride = 2ull << lo;  // floats between consecutive mids
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        float x = __uint_as_float(a[j]) + __uint_as_float(z[j]);
+                        if (j == 0 && fix0 && lane < 2) x = -x;
+                        __stcs(p, x);
+                        p += stride;
                     }
                 }
             }
-            // test hook: without the commit nothing arrives on mma_bar
-            if (!stall)
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                             ::"r"(su32(&mma_bar)) : "memory");
         }
-        mma_pending = true;
-        // ---- epilogue of the previous tile, overlapping the MMAs ----
-        if (prev != ~0ull) epilogue(prev, (it - 1) & 1u);
-        if (!mbar_wait(&mma_bar, mmas_done & 1, wait_limit)) {
-            atomicExch(status, 2);
-            s_abort = 1;
-        }
-        fence_before();
-        __syncthreads();
-        fence_after();
-        if (s_abort) break;
-        ++mmas_done;
-        mma_pending = false;
-        prev = tile;
-    }
-    if (!s_abort && prev != ~0ull) {
-        epilogue(prev, (it - 1) & 1u);
-        fence_before();
-        __syncthreads();
-    }
-    // after an abort, wait (bounded) for this CTA's own load and MMA in flight
-    // before the tensor memory is freed and the CTA exits
-    if (tid == 0) {
-        if (load_pending) (void)mbar_wait(&tma_bar, loads_done & 1, wait_limit);
-        if (mma_pending) (void)mbar_wait(&mma_bar, mmas_done & 1, wait_limit);
     }
     fence_before();
     __syncthreads();
-    if (warp == 0)
+    fence_after();
+    if (warp == kMmaWarp) {
+        __syncwarp();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kTmemCols) : "memory");
+    }
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -510,15 +521,14 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 
 // View of an n-qubit complex64 state for the pass over bits [lo, lo + kb):
-// [outer][mid][2^(lo+1) floats], box {128, 2^kb, 1}.
+// [outer][mid][2^(lo+1) floats], box {128 floats, 16 mids, 1}.
 cudaError_t encode_upper_map(CUtensorMap *m, void *amps, int n, int lo, int kb) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return cudaErrorNotSupported;
     const cuuint64_t inner = 1ull << (lo + 1);
     const cuuint64_t dims[3] = {inner, 1ull << kb, 1ull << (n - lo - kb)};
     const cuuint64_t strides[2] = {inner * 4, (inner << kb) * 4};
-    const int cols = kCols * (128 >> kb);
-    const cuuint32_t box[3] = {(cuuint32_t)(cols < 256 ? cols : 256), (cuuint32_t)(1u << kb), 1u};
+    const cuuint32_t box[3] = {(cuuint32_t)kRows, (cuuint32_t)kChunkK, 1u};
     const cuuint32_t estr[3] = {1u, 1u, 1u};
     const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, amps, dims, strides, box, estr,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -526,16 +536,16 @@ cudaError_t encode_upper_map(CUtensorMap *m, void *amps, int n, int lo, int kb) 
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-// View of the state for the lowest group: [block of 128 amplitudes][8 lines][32
-// floats], box {32, 8, 64} with the 128-byte swizzle.
+// View of the state for the lowest group: [block of 128 amplitudes][256
+// floats], box {32 floats, 64 blocks} with the 128-byte swizzle.
 cudaError_t encode_low_map(CUtensorMap *m, void *amps, int n) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return cudaErrorNotSupported;
-    const cuuint64_t dims[3] = {32, 8, 1ull << (n - 7)};
-    const cuuint64_t strides[2] = {128, 1024};
-    const cuuint32_t box[3] = {32u, 8u, (cuuint32_t)(kCols / 2)};
-    const cuuint32_t estr[3] = {1u, 1u, 1u};
-    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, amps, dims, strides, box, estr,
+    const cuuint64_t dims[2] = {256, 1ull << (n - 7)};
+    const cuuint64_t strides[1] = {1024};
+    const cuuint32_t box[2] = {32u, 64u};
+    const cuuint32_t estr[2] = {1u, 1u};
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, amps, dims, strides, box, estr,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
@@ -545,10 +555,10 @@ template <int KB, bool LOW>
 cudaError_t launch_tc_t(void *amps, int n, int lo, float scale, bool negate, int *status, long long wait_limit,
                         int stall, cudaStream_t st, const Geometry &g) {
     constexpr int K = 1 << KB;
-    // fp32 stage, three bf16 slices (128 rows), W (K rows), padded layout
-    constexpr int COLS = tile_cols<KB, LOW>();
-    const size_t smem = KB >= 6 ? (size_t)K * COLS * 4 + 3 * (size_t)COLS * K * 2 + (size_t)K * K * 2
-                                : (size_t)K * COLS * 4 + 3 * (size_t)(COLS / 8) * sbo_of(K) + (size_t)(K / 8) * sbo_of(K);
+    // stages, slots, W, barriers; at least 120 KiB so that one CTA runs per
+    // SM (each allocates all 512 TMEM columns)
+    size_t smem = (size_t)kRing * kStageBytes + (size_t)kSlots * kSlotBytes + (size_t)K * K * 2 + sizeof(TcShared);
+    if (smem < 120 * 1024) smem = 120 * 1024;
     auto kern = k_wht_tc<KB, LOW>;
     {
         cudaError_t e = raise_smem_limit(kern, smem);
@@ -560,8 +570,7 @@ cudaError_t launch_tc_t(void *amps, int n, int lo, float scale, bool negate, int
         cudaError_t e = LOW ? encode_low_map(&tmap, amps, n) : encode_upper_map(&tmap, amps, n, lo, KB);
         if (e != cudaSuccess) return e;
     }
-    const uint64_t N = 1ull << n;
-    const uint64_t ntiles = N / ((uint64_t)(COLS / 2) * K);
+    const uint64_t ntiles = (1ull << n) / 8192ull;
     const uint64_t grid = ntiles < (uint64_t)g.sm_count ? ntiles : (uint64_t)g.sm_count;
     kern<<<(unsigned)grid, kTcThreads, smem, st>>>(static_cast<float *>(amps), tmap, lo, ntiles, scale,
                                                    negate ? 1 : 0, status, wait_limit, stall);
