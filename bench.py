@@ -405,7 +405,8 @@ def run_ours(args):
     gate = None
     if args.gate_iters > 0:
         gate = {"iterations_timed": args.gate_iters, "unit": UNIT}
-        engines = [("tensor_cores", 1), ("cuda_cores", 0)] if (dtype == "c64" and n >= 13) else [("cuda_cores", 0)]
+        engines = ([("tensor_cores", 1), ("cuda_cores", 0), ("default", -1)] if (dtype == "c64" and n >= 13)
+                   else [("cuda_cores", 0)])
         for name, eng in engines:
             st.set_gate_engine(eng)
             st.init_uniform()
@@ -418,10 +419,14 @@ def run_ours(args):
             torch.cuda.synchronize()
             st.sync()
             gate_s = g0.elapsed_time(g1) / 1e3 / args.gate_iters
-            groups = gate_groups(n, eng == 1)
+            groups, on_tc = gate_engine_groups(n, eng) if dtype == "c64" else (gate_groups(n, False), False)
             passes = 2 * len(groups)
             gate[name] = {"iteration_ms": gate_s * 1e3, "value": N / gate_s, "passes_per_iteration": passes,
-                          "group_bits": groups, "hbm_gbs": passes * 2 * BYTES_PER_AMP[dtype] * N / gate_s / 1e9,
+                          "group_bits": groups,
+                          "tensor_core_groups": [kb for i, kb in enumerate(groups)
+                                                 if on_tc and tc_pass_supported(n, sum(groups[:i]), kb)],
+                          "hbm_gbs": passes * 2 * BYTES_PER_AMP[dtype] * N / gate_s / 1e9,
+                          "hbm_frac": passes * 2 * BYTES_PER_AMP[dtype] * N / gate_s / 1e9 / measured_peaks()[0]["hbm_gbs"],
                           "operator_speedup": gate_s / pass_s}
         st.set_gate_engine(-1)
         # gate by gate (one pass per single-qubit gate, Fig. oracle1 oracle):
@@ -539,6 +544,22 @@ def tc_pass_supported(n, lo, kb):
     if lo == 0:
         return kb == 7 and n >= 13
     return 5 <= kb <= 7 and lo >= 13 - kb and lo + kb <= n
+
+
+GATE_TC_AUTO_MIN_QUBITS = 26
+
+
+def gate_engine_groups(n, engine):
+    """(group sizes, tensor cores used) of grover_iterate_gate for a complex64
+    state (grover.h, GROVER_OPT_GATE_ENGINE): 0 CUDA cores, 1 tensor cores,
+    -1 the default (CUDA cores below n = 26, else the plan with fewer groups,
+    ties to the 7-bit one, tensor cores on every group they take)."""
+    if engine == 1:
+        return gate_groups(n, True), True
+    if engine == 0 or n < GATE_TC_AUTO_MIN_QUBITS:
+        return gate_groups(n, False), False
+    t, c = gate_groups(n, True), gate_groups(n, False)
+    return (t if len(t) <= len(c) else c), True
 
 
 def gate_groups(n, tensor_cores):
@@ -950,7 +971,7 @@ def run_gate_kernels(args):
     mk = binding.Marked(n, inputs.marked_indices(n, m, seed))
     stream = torch.cuda.current_stream()
     out = {"study": "gate-kernels", "workload": f"n={n} complex64, M={m} (seed {seed}), uniform start"}
-    for name, eng in (("tensor_cores", 1), ("cuda_cores", 0)):
+    for name, eng in (("tensor_cores", 1), ("cuda_cores", 0), ("default", -1)):
         st = binding.State(n, "c64", stream=stream)
         st.set_gate_engine(eng)
         st.init_uniform()
@@ -958,9 +979,9 @@ def run_gate_kernels(args):
             st.iterate_gate(mk, 1)
         t = _timed_events(lambda: st.iterate_gate(mk, 1), args.steps, stream)
         st.sync()
-        groups = gate_groups(n, eng == 1)
+        groups, on_tc = gate_engine_groups(n, eng)
         passes = 2 * len(groups)
-        out[name] = {"iteration_ms": t * 1e3, "groups": groups, "passes": passes,
+        out[name] = {"iteration_ms": t * 1e3, "groups": groups, "tensor_cores": on_tc, "passes": passes,
                      "pass_gbs": passes * 16 * N / t / 1e9}
         del st
     return out

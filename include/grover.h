@@ -133,11 +133,17 @@ typedef enum {
      *       (GROVER_EUNSUPPORTED where neither fits);
      *    2: the grid iterator (GROVER_EUNSUPPORTED where it does not fit). */
     GROVER_OPT_RESIDENT = 0,
-    /* Engine of grover_iterate_gate's Walsh-Hadamard passes: -1 (default) and
-     * 0 CUDA cores (the passes are bandwidth-bound; on GB300 the CUDA-core
-     * passes measured 1.1-3.3x faster than the tensor-core ones at every
-     * n = 13..30); 1 the tensor cores (GROVER_EUNSUPPORTED for complex128 or
-     * n < 13). */
+    /* Engine of grover_iterate_gate's Walsh-Hadamard passes.
+     *    0: CUDA cores, ceil(n/8) groups of balanced sizes;
+     *    1: tensor cores, 7-bit groups (complex64; GROVER_EUNSUPPORTED for
+     *       complex128 or n < 13); a group the tensor-core pass does not take
+     *       (fewer than 5 bits above bit 0) runs on CUDA cores;
+     *   -1 (default): complex64 with n >= 26: whichever of the two group plans
+     *       has fewer groups (ties: the 7-bit one), every group of at most 7
+     *       bits on the tensor cores and the 8-bit ones on CUDA cores; else
+     *       CUDA cores.  Measured on GB300: at n >= 26 a tensor-core pass moves
+     *       6.3-6.7 TB/s against 5.7-6.2 for a CUDA-core one; below, it has
+     *       fewer tiles than its pipeline needs and is 1.4-3x slower. */
     GROVER_OPT_GATE_ENGINE = 1,
     /* Polls (about 0.1 us each) a bounded device-side wait makes before it
      * gives up; default 2^22.  A wait that gives up sets the device status
@@ -230,10 +236,10 @@ grover_status grover_iterate(grover_state *s, const grover_marked *mk, uint64_t 
  * one read + write pass over the state per group, with exact power-of-two
  * scaling (2^-n per iteration in total); the phase shift is fused into the
  * last pass of the first transform.  Engines (GROVER_OPT_GATE_ENGINE): the
- * tensor cores (complex64: 7-bit groups as dense +-1 matrix products,
- * operands split into three bf16 slices, FP32 accumulation) or CUDA cores
- * (ceil(n/8) groups of balanced sizes, +-1 butterflies; the default).  The
- * result equals grover_iterate's up to
+ * tensor cores (complex64: groups of 5-7 bits as dense +-1 matrix products,
+ * operands split into three bf16 slices, FP32 accumulation) and CUDA cores
+ * (+-1 butterflies); by default the tensor cores for complex64 states of
+ * 2^26 amplitudes or more.  The result equals grover_iterate's up to
  * rounding (no global phase).  Invalidates the cached mean; a tensor-core wait
  * that gives up is reported by grover_sync (GROVER_ETIMEOUT). */
 grover_status grover_iterate_gate(grover_state *s, const grover_marked *mk, uint64_t k);

@@ -174,8 +174,9 @@ class State:
         _check(lib().grover_set_option(self.handle, 0, int(value)), self.handle)
 
     def set_gate_engine(self, value: int):
-        """-1 automatic (CUDA cores), 0 CUDA-core butterflies, 1 tensor cores
-        (complex64, n >= 13)."""
+        """-1 automatic (complex64 from n = 26: tensor cores on every group of
+        at most 7 bits), 0 CUDA-core butterflies, 1 tensor cores (complex64,
+        n >= 13)."""
         _check(lib().grover_set_option(self.handle, 1, int(value)), self.handle)
 
     def set_staged(self, value: int):

@@ -532,45 +532,55 @@ grover_status grover_iterate_gate(grover_state *s, const grover_marked *mk, uint
     if (grover_status st = check_state(s)) return st;
     if (grover_status st = check_marked(s, mk)) return st;
     if (k == 0) return GROVER_OK;
-    // CUDA cores (default; measured faster than the tensor cores at every n):
-    // ceil(n / 8) groups of balanced sizes (a 1-bit remainder group would cost
-    // a whole pass for one butterfly stage); tensor cores (asked for):
-    // complex64, 7-bit groups from bit 0 (needs n >= 13), the last one
-    // shorter, CUDA cores for any group the tensor-core pass does not cover
+    // Plans: CUDA cores take ceil(n / 8) index-bit groups of balanced sizes;
+    // tensor cores 7 bits from bit 0 and the rest in 7-bit groups, or in
+    // near-equal groups where that leaves fewer groups the tensor-core pass
+    // cannot take.  Engine 0: the CUDA-core plan, all on CUDA cores.  Engine
+    // 1: the tensor-core plan, every group the tensor-core pass takes on the
+    // tensor cores, the rest on CUDA cores.  Default (-1): CUDA cores below
+    // 2^26 complex64 amplitudes (there a tensor-core pass has fewer tiles than
+    // its pipeline needs and measured slower); from 2^26 on, whichever plan
+    // has fewer groups (ties: the tensor-core plan), with every group the
+    // tensor-core pass takes on the tensor cores.
     const bool tc_possible = s->dtype == GROVER_C64 && s->n >= 13;
     if (s->gate_engine == 1 && !tc_possible)
         return fail(s, GROVER_EUNSUPPORTED, "the tensor-core gate path needs a complex64 state with n >= 13");
-    const bool tc = tc_possible && s->gate_engine == 1;
-    const int gbits = tc ? 7 : 8;
-    const int ngroups = (s->n + gbits - 1) / gbits;
-    int glo[8], gkb[8];  // n <= 33: at most 5 groups
-    for (int gi = 0, lo = 0; gi < ngroups; ++gi) {
-        const int kb = tc ? (s->n - lo < gbits ? s->n - lo : gbits) : s->n / ngroups + (gi < s->n % ngroups ? 1 : 0);
-        glo[gi] = lo;
-        gkb[gi] = kb;
-        lo += kb;
+    int clo[8], ckb[8], tlo[8], tkb[8];  // n <= 33: at most 5 groups
+    const int ncc = (s->n + 7) / 8;
+    for (int gi = 0, lo = 0; gi < ncc; ++gi) {
+        ckb[gi] = s->n / ncc + (gi < s->n % ncc ? 1 : 0);
+        clo[gi] = lo;
+        lo += ckb[gi];
     }
-    if (tc) {
-        // 7 bits from bit 0, then the rest in near-equal groups (largest
-        // first) where that leaves fewer groups the tensor-core pass cannot
-        // take than the greedy split's short remainder does
+    int ntc = 0;
+    if (tc_possible) {
+        ntc = (s->n + 6) / 7;
+        for (int gi = 0, lo = 0; gi < ntc; ++gi) {
+            tkb[gi] = s->n - lo < 7 ? s->n - lo : 7;
+            tlo[gi] = lo;
+            lo += tkb[gi];
+        }
         auto fallbacks = [&](const int *kbs) {
             int c = 0;
-            for (int gi = 0, lo = 0; gi < ngroups; lo += kbs[gi], ++gi) c += !tc_pass_supported(s->n, lo, kbs[gi]);
+            for (int gi = 0, lo = 0; gi < ntc; lo += kbs[gi], ++gi) c += !tc_pass_supported(s->n, lo, kbs[gi]);
             return c;
         };
-        const int rest = s->n - 7, parts = ngroups - 1;
+        const int rest = s->n - 7, parts = ntc - 1;
         if (parts > 0) {
             int bal[8];
             bal[0] = 7;
             for (int j = 0; j < parts; ++j) bal[j + 1] = rest / parts + (j < rest % parts ? 1 : 0);
-            if (fallbacks(bal) < fallbacks(gkb))
-                for (int gi = 0, lo = 0; gi < ngroups; lo += bal[gi], ++gi) {
-                    glo[gi] = lo;
-                    gkb[gi] = bal[gi];
+            if (fallbacks(bal) < fallbacks(tkb))
+                for (int gi = 0, lo = 0; gi < ntc; lo += bal[gi], ++gi) {
+                    tlo[gi] = lo;
+                    tkb[gi] = bal[gi];
                 }
         }
     }
+    const bool use_tc = s->gate_engine == 1 || (s->gate_engine < 0 && tc_possible && s->n >= kGateTcAutoMinQubits);
+    const bool tc_plan = s->gate_engine == 1 || (use_tc && ntc <= ncc);
+    const int ngroups = tc_plan ? ntc : ncc;
+    const int *glo = tc_plan ? tlo : clo, *gkb = tc_plan ? tkb : ckb;
     s->mu_valid = false;
     for (uint64_t t = 0; t < k; ++t) {
         CK(s, launch_oracle(s->amps, s->n, s->dtype, mk->dev, s->stream, s->geo), "oracle launch");
@@ -578,7 +588,7 @@ grover_status grover_iterate_gate(grover_state *s, const grover_marked *mk, uint
             const int gi = pass % ngroups, lo = glo[gi], kb = gkb[gi];
             const bool first = pass < ngroups;  // first H^{(x)n}: scaled by 2^-n in total
             const bool phase = pass == ngroups - 1;
-            if (tc && tc_pass_supported(s->n, lo, kb)) {
+            if (use_tc && tc_pass_supported(s->n, lo, kb)) {
                 const int stall = s->test_stall;
                 s->test_stall = 0;
                 CK(s, launch_wht_tc_pass(s->amps, s->n, lo, kb, first, phase, s->sc.status, s->wait_limit, stall,

@@ -158,6 +158,8 @@ cudaError_t launch_wht_pass(void *amps, int n, grover_dtype dt, int lo, int kb, 
 // ---- conventional circuit on tensor cores (k_gate_tc.cu), complex64 ---------
 // true if a tensor-core pass exists for bits [lo, lo + kb) of an n-qubit state
 bool tc_pass_supported(int n, int lo, int kb);
+// smallest n whose default gate path uses the tensor cores
+constexpr int kGateTcAutoMinQubits = 26;
 // Walsh-Hadamard pass on the tensor cores; a wait longer than wait_limit
 // polls gives up and sets *status = 2; stall != 0 withholds the MMA
 // completion signal (test hook for that path)

@@ -52,16 +52,32 @@ def groups(n, tensor_cores):
     return [n // g + (1 if i < n % g else 0) for i in range(g)]
 
 
+TC_AUTO_MIN_QUBITS = 26  # smallest n whose default gate path uses the tensor cores
+
+
+def engine_groups(n, engine):
+    """(group sizes, tensor cores used) of grover_iterate_gate for a complex64
+    state: engine 0 CUDA cores, 1 tensor cores, -1 the default (CUDA cores
+    below n = 26; from there the plan with fewer groups, ties to the 7-bit
+    one, with the tensor cores on every group they take)."""
+    if engine in (True, 1):
+        return groups(n, True), True
+    if engine in (False, 0) or n < TC_AUTO_MIN_QUBITS:
+        return groups(n, False), False
+    t, c = groups(n, True), groups(n, False)
+    return (t if len(t) <= len(c) else c), True
+
+
 def pass_plan(n, tensor_cores):
-    """[(lo, kb, on_tensor_cores, scaled, phase_shift_after)] of one iteration."""
-    gs = groups(n, tensor_cores)
+    """[(lo, kb, on_tensor_cores, scaled, phase_shift_after)] of one iteration;
+    tensor_cores: True / 1, False / 0, or -1 for the default engine."""
+    gs, tc = engine_groups(n, tensor_cores)
     los = [sum(gs[:i]) for i in range(len(gs))]
     plan = []
     for p in range(2 * len(gs)):
         gi = p % len(gs)
         lo, kb = los[gi], gs[gi]
-        plan.append((lo, kb, bool(tensor_cores and tc_pass_supported(n, lo, kb)), p < len(gs),
-                     p == len(gs) - 1))
+        plan.append((lo, kb, bool(tc and tc_pass_supported(n, lo, kb)), p < len(gs), p == len(gs) - 1))
     return plan
 
 
@@ -242,7 +258,7 @@ def exact_input(n, tensor_cores=True):
     iteration the gate path must return -x bit for bit.  A split keeping two
     slices sees C + 1 in place of C."""
     x = np.ones(1)
-    for kb in groups(n, tensor_cores):
+    for kb in engine_groups(n, tensor_cores)[0]:
         x = np.kron(exact_factor(kb), x)  # lower groups vary fastest
     return x * (EXACT_C * EXACT_SCALE) * (1.0 + 0.5j)
 

@@ -162,6 +162,37 @@ def test_gate_exact_input(B, engine, n):
     assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(x))
 
 
+@pytest.mark.parametrize("n", [26, 29])
+def test_gate_default_engine_exact_input(B, n):
+    """The default engine at sizes where it uses the tensor cores: n = 26 (the
+    7-bit plan, all four groups on the tensor cores) and n = 29 (the 8-bit
+    plan has fewer groups: 8, 7, 7, 7, the 7-bit ones on the tensor cores, the
+    8-bit one on CUDA cores).  Same exact input and closed form (-x, then +x)
+    as test_gate_exact_input; the input is built on the device."""
+    free, _ = torch.cuda.mem_get_info()
+    if free < (4 << 30) + 2 * (8 << n):
+        pytest.skip("not enough free device memory")
+    plan = gate_model.pass_plan(n, -1)
+    assert any(tc for _lo, _kb, tc, _s, _p in plan)
+    if n == 29:
+        assert any(not tc for _lo, _kb, tc, _s, _p in plan)
+    x = torch.ones(1, dtype=torch.complex64, device="cuda")
+    for kb in gate_model.engine_groups(n, -1)[0]:
+        f = torch.as_tensor(gate_model.exact_factor(kb), dtype=torch.complex64, device="cuda")
+        x = torch.kron(f, x)
+    x *= complex(gate_model.EXACT_C * gate_model.EXACT_SCALE) * (1.0 + 0.5j)
+    mk = B.Marked(n, gate_model.exact_marked(n))
+    st = B.State(n, "c64")
+    st.init_state(x)
+    for sign in (-1.0, 1.0):
+        st.iterate_gate(mk, 1)
+        st.sync()
+        torch.cuda.synchronize()
+        assert torch.equal(st.amps, sign * x)
+    del st
+    torch.cuda.empty_cache()
+
+
 def test_gate_tensor_cores_uniform_success(B):
     n, m = 16, 1
     marked = inputs.marked_indices(n, m, seed=7)
