@@ -613,6 +613,7 @@ def run_batched(args):
     stream = torch.cuda.current_stream()
     b = binding.Batch(ns, ks, marks, stream=stream)
     threads, onchip = b.tune()
+    pack_size, pack_min = b.packing()
     for _ in range(args.warmup):
         b.run()
     b.success()
@@ -669,13 +670,16 @@ def run_batched(args):
         sn, sk, sm_ = [ns[i] for i in sub], [ks[i] for i in sub], [marks[i] for i in sub]
         b3 = binding.Batch(sn, sk, sm_, stream=stream)
         th3, oc3 = b3.tune()
+        pk3 = b3.packing()
         for _ in range(2):
             b3.run()
         t3 = _timed_events(b3.run, max(1, min(args.steps, 5)), stream)
         b3.close()
         units3 = float(sum((1 << n) * k for n, k in zip(sn, sk)))
         rec = {"instances": len(sub), "n_range": [min(sn), max(sn)], "ms_per_launch": t3 * 1e3,
-               "value": units3 / t3, "unit": UNIT, "tuned": {"threads": th3, "onchip_vecs": oc3}}
+               "value": units3 / t3, "unit": UNIT,
+               "tuned": {"threads": th3, "onchip_vecs": oc3, "cluster_size": pk3[0],
+                         "cluster_min_qubits": pk3[1] if pk3[0] > 1 else None}}
         if part == "onchip":
             rec["roofline"] = smem_roofline(
                 16.0 * units3, t3, "k_batch (instances in shared memory)", sm_count, sm_mhz,
@@ -686,7 +690,8 @@ def run_batched(args):
             rec["roofline"]["iteration_us"] = None
         else:
             rec["roofline"] = hbm_roofline(
-                sum(16 * (1 << n) * k + 8 * (1 << n) for n, k in zip(sn, sk)), t3, "k_batch (streamed instances)",
+                sum(16 * (1 << n) * k + 8 * (1 << n) for n, k in zip(sn, sk)), t3,
+                "k_batch (streamed instances)" + (f" + k_batch_cluster (n >= {pk3[1]})" if pk3[0] > 1 else ""),
                 peaks, peak_src)
         parts[part] = rec
     return {
@@ -696,7 +701,8 @@ def run_batched(args):
         "config": {"workload": "batched: 4096 independent searches, n ~ U[8,20], M ~ U[1,8], k_i optimal, "
                                "complex64, one persistent CUDA-graph launch per step", "name": "batched-4096",
                    "instances": len(ns), "amp_updates_per_step": units / args.steps,
-                   "tuned": {"threads": threads, "onchip_vecs": onchip},
+                   "tuned": {"threads": threads, "onchip_vecs": onchip, "cluster_size": pack_size,
+                             "cluster_min_qubits": pack_min if pack_size > 1 else None},
                    "l2": "per-step traffic 16 B x N x k of the streamed instances (> L2 in total)",
                    "parallelism": f"replicas x{world}"},
         "roofline": dict(hbm_roofline(hbm, t_max / args.steps, "k_batch", peaks, peak_src),

@@ -52,6 +52,8 @@ _SIGS = {
     "grover_batch_run": (ctypes.c_int, [_vp]),
     "grover_batch_tune": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_uint32)]),
     "grover_batch_set_packing": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "grover_batch_set_packing_min_qubits": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "grover_batch_get_packing": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "grover_batch_success": (ctypes.c_int, [_vp, _vp]),
     "grover_batch_destroy": (ctypes.c_int, [_vp]),
     "grover_phase_forward": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_uint64, _vp]),
@@ -310,9 +312,18 @@ class Batch:
         _check(lib().grover_batch_tune(self.handle, ctypes.byref(th), ctypes.byref(oc)))
         return th.value, oc.value
 
-    def set_packing(self, cluster_size: int):
-        """16: clusters of 16 CTAs for instances with n >= 17; 0 or 1: one CTA each."""
+    def set_packing(self, cluster_size: int, min_qubits: int | None = None):
+        """16: clusters of 16 CTAs for instances with n >= min_qubits (17 by
+        default); 0 or 1: one CTA each."""
+        if min_qubits is not None:
+            _check(lib().grover_batch_set_packing_min_qubits(self.handle, int(min_qubits)))
         _check(lib().grover_batch_set_packing(self.handle, int(cluster_size)))
+
+    def packing(self):
+        """(cluster size, threshold in qubits) in use."""
+        cs, mq = ctypes.c_int(), ctypes.c_int()
+        _check(lib().grover_batch_get_packing(self.handle, ctypes.byref(cs), ctypes.byref(mq)))
+        return cs.value, mq.value
 
     def success(self):
         p = np.empty(self.count, dtype=np.float64)

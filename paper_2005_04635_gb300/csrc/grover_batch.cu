@@ -28,6 +28,7 @@ struct grover_batch {
     unsigned grid;
     int clusters;           // co-resident clusters (0: cluster packing unavailable)
     int packing;            // 0: one CTA per instance; kBatchClusterSize: clusters for large instances
+    int pack_min_qubits;    // with packing: instances of at least this many qubits run on clusters
     uint32_t *order_dev;    // [2 * count]: small order, then large order
     std::vector<uint32_t> order;  // all instances, largest N * k first
     std::vector<int> nq;    // qubits per instance
@@ -59,7 +60,7 @@ grover_status bfail(grover_batch *b, grover_status st, const char *msg, cudaErro
 grover_status split(grover_batch *b) {
     const bool use = b->packing > 1 && b->clusters > 0;
     std::vector<uint32_t> small, large;
-    for (uint32_t i : b->order) ((use && b->nq[i] >= kBatchClusterMinQubits) ? large : small).push_back(i);
+    for (uint32_t i : b->order) ((use && b->nq[i] >= b->pack_min_qubits) ? large : small).push_back(i);
     cudaError_t e = cudaSuccess;
     if (!small.empty())
         e = cudaMemcpy(b->order_dev, small.data(), small.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
@@ -203,6 +204,7 @@ grover_status grover_batch_create(grover_batch **out, size_t count, const int *n
         b->clusters = 0;
     }
     b->packing = 0;  // one CTA per instance; grover_batch_tune also tries clusters
+    b->pack_min_qubits = kBatchClusterMinQubits;
     if ((e = cudaMemcpy((void *)L.inst, inst.data(), count * sizeof(BatchInst), cudaMemcpyHostToDevice)) !=
             cudaSuccess ||
         (total_marked && (e = cudaMemcpy((void *)L.marked, marked, total_marked * sizeof(uint64_t),
@@ -282,19 +284,38 @@ grover_status grover_batch_tune(grover_batch *b, int *threads_out, uint32_t *onc
                    cudaGraphLaunch(b->exec, b->stream) == cudaSuccess && cudaEventRecord(e1, b->stream) == cudaSuccess &&
                    cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(ms, e0, e1) == cudaSuccess;
         };
-        float t_one = 0.f, t_cluster = 0.f;
-        const bool ok1 = time_graph(&t_one);
-        b->packing = kBatchClusterSize;
-        grover_status st = rebuild(b);
-        const bool ok2 = st == GROVER_OK && time_graph(&t_cluster);
-        if (!ok1 || !ok2 || t_cluster >= t_one) {
-            (void)cudaGetLastError();
-            b->packing = 0;
-            if ((st = rebuild(b)) != GROVER_OK) {
-                cudaEventDestroy(e0);
-                cudaEventDestroy(e1);
-                return st;
+        // clusters for the instances of at least 17 or at least 19 qubits
+        // (17-18 qubits fit the clusters' shared memory, 19-20 stream through
+        // L2), or none
+        float t_best = 0.f;
+        const bool ok1 = time_graph(&t_best);
+        int best_min = 0;
+        grover_status st = GROVER_OK;
+        if (ok1) {
+            static const int kMinOpts[] = {kBatchClusterMinQubits, kBatchClusterMinQubits + 2};
+            int nmax = 0;
+            for (int q : b->nq) nmax = q > nmax ? q : nmax;
+            for (int mq : kMinOpts) {
+                if (mq > nmax) continue;  // no instance would change place
+                b->packing = kBatchClusterSize;
+                b->pack_min_qubits = mq;
+                float t = 0.f;
+                st = rebuild(b);
+                if (st == GROVER_OK && time_graph(&t) && t < t_best) {
+                    t_best = t;
+                    best_min = mq;
+                }
+                (void)cudaGetLastError();
             }
+        } else {
+            (void)cudaGetLastError();
+        }
+        b->packing = best_min ? kBatchClusterSize : 0;
+        b->pack_min_qubits = best_min ? best_min : kBatchClusterMinQubits;
+        if ((st = rebuild(b)) != GROVER_OK) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return st;
         }
     }
     cudaEventDestroy(e0);
@@ -312,6 +333,21 @@ grover_status grover_batch_set_packing(grover_batch *b, int cluster_size) {
         return bfail(b, GROVER_EUNSUPPORTED, "clusters of 16 CTAs cannot run on this device");
     b->packing = cluster_size;
     return rebuild(b);
+}
+
+grover_status grover_batch_set_packing_min_qubits(grover_batch *b, int min_qubits) {
+    if (!b) return bfail(nullptr, GROVER_EINVAL, "batch is NULL");
+    if (min_qubits < kBatchClusterMinQubits || min_qubits > kBatchMaxQubits)
+        return bfail(b, GROVER_EINVAL, "the packing threshold must be in [17, 26] qubits");
+    b->pack_min_qubits = min_qubits;
+    return rebuild(b);
+}
+
+grover_status grover_batch_get_packing(const grover_batch *b, int *cluster_size, int *min_qubits) {
+    if (!b) return bfail(nullptr, GROVER_EINVAL, "batch is NULL");
+    if (cluster_size) *cluster_size = b->packing > 1 ? b->packing : 1;
+    if (min_qubits) *min_qubits = b->pack_min_qubits;
+    return GROVER_OK;
 }
 
 grover_status grover_batch_success(grover_batch *b, double *p_success) {

@@ -354,16 +354,26 @@ __global__ void __launch_bounds__(kBcThreads, 1) k_batch_cluster(BatchClusterLau
                 }
                 r = warp_sum_i192(r);
                 i = warp_sum_i192(i);
-                if (__any_sync(0xffffffffu, side)) {
+                const int side_any = __any_sync(0xffffffffu, side);
+                if (side_any) {
                     xr = warp_sum_d(xr);
                     xi = warp_sum_d(xi);
                 }
                 if (lane == 0) {
-                    const double inv_n = ldexp(1.0, -I.n);
-                    const double tr = 2.0 * ((i192_to_double(r) * 0x1p-100 + xr) * inv_n);
-                    const double ti = 2.0 * ((i192_to_double(i) * 0x1p-100 + xi) * inv_n);
-                    const float hr = (float)tr, hi = (float)ti;
-                    s_two = make_float4(hr, (float)(tr - (double)hr), hi, (float)(ti - (double)hi));
+                    if (!side_any) {
+                        // 2 mu = total 2^(1 - 100 - n) as a float pair, formed with
+                        // integer operations from the exact total (which fits 128
+                        // bits): no FP64 latency on the iteration's critical path
+                        const float2 pr = fix_to_f32_pair(((u128)r.w1 << 64) | r.w0, -99 - I.n);
+                        const float2 pi = fix_to_f32_pair(((u128)i.w1 << 64) | i.w0, -99 - I.n);
+                        s_two = make_float4(pr.x, pr.y, pi.x, pi.y);
+                    } else {
+                        const double inv_n = ldexp(1.0, -I.n);
+                        const double tr = 2.0 * ((i192_to_double(r) * 0x1p-100 + xr) * inv_n);
+                        const double ti = 2.0 * ((i192_to_double(i) * 0x1p-100 + xi) * inv_n);
+                        const float hr = (float)tr, hi = (float)ti;
+                        s_two = make_float4(hr, (float)(tr - (double)hr), hi, (float)(ti - (double)hi));
+                    }
                 }
             }
             __syncthreads();

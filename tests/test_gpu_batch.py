@@ -93,15 +93,16 @@ def test_batch_rejects_bad_input(B):
         B.Batch([10], [3], [list(range(65))])  # more than 64 marked
 
 
-@pytest.mark.parametrize("packing", [16, 0])
-def test_batch_large_instances_both_packings(B, packing):
-    """Instances with n = 15..20 (clusters of 16 CTAs for n >= 17: on chip up to
-    n = 18, streamed through L2 above), mixed with small ones, against the
-    closed form under both packings."""
+@pytest.mark.parametrize("packing,min_qubits", [(16, 17), (16, 19), (0, 17)])
+def test_batch_large_instances_both_packings(B, packing, min_qubits):
+    """Instances with n = 15..20 (clusters of 16 CTAs for n >= 17 or n >= 19:
+    on chip up to n = 18, streamed through L2 above), mixed with small ones,
+    against the closed form under each packing."""
     ns, ks, marks = make_instances(40, 15, 20, 8, seed=31)
     ns2, ks2, marks2 = make_instances(40, 3, 12, 8, seed=32)
     b = B.Batch(ns + ns2, ks + ks2, marks + marks2)
-    b.set_packing(packing)
+    b.set_packing(packing, min_qubits)
+    assert b.packing() == (packing if packing > 1 else 1, min_qubits)
     b.run()
     p = b.success()
     torch.cuda.synchronize()
@@ -118,4 +119,7 @@ def test_batch_packing_rejects_bad_size(B):
     b = B.Batch([5], [2], [[3]])
     with pytest.raises(B.GroverError) as ei:
         b.set_packing(8)
+    assert ei.value.status == 1
+    with pytest.raises(B.GroverError) as ei:
+        b.set_packing(16, 16)  # threshold below 17 qubits
     assert ei.value.status == 1
