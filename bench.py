@@ -650,48 +650,66 @@ def run_batched(args):
         theta = math.atan2(math.sqrt(len(mk)), math.sqrt((1 << n) - len(mk)))
         worst = max(worst, abs(pi - math.sin((2 * k + 1) * theta) ** 2))
     # HBM bytes: streamed instances read + write every iteration; on-chip ones
-    # are written once at the end
+    # (one CTA, or a group of CTAs) are written once at the end
     onchip_amps = 2 * onchip
-    hbm = sum(16 * (1 << n) * k + 8 * (1 << n) if (1 << n) > onchip_amps else 8 * (1 << n) for n, k in zip(ns, ks))
+    sm_count0 = torch.cuda.get_device_properties(0).multi_processor_count
+
+    def on_chip(n):
+        return (1 << n) <= onchip_amps or (pack_size == 2 and n >= pack_min and (1 << n) * 8 <= sm_count0 * 226 * 1024)
+    hbm = sum(8 * (1 << n) if on_chip(n) else 16 * (1 << n) * k + 8 * (1 << n) for n, k in zip(ns, ks))
     peaks, peak_src = measured_peaks()
     achieved = hbm * args.steps / t_max / 1e9
     h2d = 4 * len(ns) + 8 * len(ns) + 8 * sum(len(x) for x in marks) + 8 * (len(ns) + 1)
-    # the two classes of instances, each timed alone against its own bound: the
-    # ones the tuned threshold keeps in shared memory (bytes read + written
-    # there per iteration) and the ones streamed through L2 / HBM
+    # the classes of instances, each timed alone (same kernel choices) against
+    # its own bound: one CTA per instance in shared memory (n up to the tuned
+    # on-chip size), groups of CTAs holding the state in shared memory (the
+    # packing chosen by the tuner), and the rest streamed through L2 / HBM
     sm_count = torch.cuda.get_device_properties(0).multi_processor_count
     sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz") or 2070.0
+    group_ok = lambda n: n >= pack_min and (1 << n) * 8 <= sm_count * 226 * 1024
+    cls_of = {}
+    for i, n in enumerate(ns):
+        if (1 << n) <= onchip_amps:
+            cls_of[i] = "onchip"
+        elif pack_size == 2 and group_ok(n):
+            cls_of[i] = "groups"
+        elif pack_size == 16 and n >= max(pack_min, 17):
+            cls_of[i] = "clusters"
+        else:
+            cls_of[i] = "streamed"
     parts = {}
-    for part, sel in (("onchip", [(1 << n) <= onchip_amps for n in ns]),
-                      ("streamed", [(1 << n) > onchip_amps for n in ns])):
-        sub = [i for i, f in enumerate(sel) if f]
+    for part in ("onchip", "groups", "clusters", "streamed"):
+        sub = [i for i in range(len(ns)) if cls_of[i] == part]
         if not sub:
             continue
         sn, sk, sm_ = [ns[i] for i in sub], [ks[i] for i in sub], [marks[i] for i in sub]
         b3 = binding.Batch(sn, sk, sm_, stream=stream)
         th3, oc3 = b3.tune()
-        pk3 = b3.packing()
+        b3.set_packing(pack_size, pack_min)
         for _ in range(2):
             b3.run()
         t3 = _timed_events(b3.run, max(1, min(args.steps, 5)), stream)
         b3.close()
         units3 = float(sum((1 << n) * k for n, k in zip(sn, sk)))
         rec = {"instances": len(sub), "n_range": [min(sn), max(sn)], "ms_per_launch": t3 * 1e3,
-               "value": units3 / t3, "unit": UNIT,
-               "tuned": {"threads": th3, "onchip_vecs": oc3, "cluster_size": pk3[0],
-                         "cluster_min_qubits": pk3[1] if pk3[0] > 1 else None}}
-        if part == "onchip":
+               "value": units3 / t3, "unit": UNIT, "tuned_one_cta": {"threads": th3, "onchip_vecs": oc3}}
+        if part in ("onchip", "groups"):
             rec["roofline"] = smem_roofline(
-                16.0 * units3, t3, "k_batch (instances in shared memory)", sm_count, sm_mhz,
-                "one CTA per instance keeps its state in shared memory for all k_i iterations; bytes = 16 per "
-                "amplitude-update (read + write in shared memory); algorithmic_bytes_per_iteration is the whole "
-                "class's per launch")
-            rec["roofline"]["algorithmic_bytes_per_iteration"] = 16.0 * units3
+                16.0 * units3, t3,
+                "k_batch (instances in shared memory)" if part == "onchip" else
+                f"k_batch_group (groups of CTAs, n >= {pack_min})", sm_count, sm_mhz,
+                "the states stay in shared memory for all k_i iterations; bytes = 16 per amplitude-update (read + "
+                "write in shared memory), the whole class per launch" +
+                ("; per iteration the CTAs of a group exchange exact partial sums through global memory, which "
+                 "bounds the iteration" if part == "groups" else ""))
+            rec["roofline"]["algorithmic_bytes_per_iteration"] = None
             rec["roofline"]["iteration_us"] = None
+            rec["roofline"]["algorithmic_bytes_per_launch"] = 16.0 * units3
+            rec["hbm_equivalent_gbs"] = 16.0 * units3 / t3 / 1e9
         else:
             rec["roofline"] = hbm_roofline(
                 sum(16 * (1 << n) * k + 8 * (1 << n) for n, k in zip(sn, sk)), t3,
-                "k_batch (streamed instances)" + (f" + k_batch_cluster (n >= {pk3[1]})" if pk3[0] > 1 else ""),
+                "k_batch (streamed instances)" if part == "streamed" else f"k_batch_cluster (n >= {pack_min})",
                 peaks, peak_src)
         parts[part] = rec
     return {
@@ -701,13 +719,17 @@ def run_batched(args):
         "config": {"workload": "batched: 4096 independent searches, n ~ U[8,20], M ~ U[1,8], k_i optimal, "
                                "complex64, one persistent CUDA-graph launch per step", "name": "batched-4096",
                    "instances": len(ns), "amp_updates_per_step": units / args.steps,
-                   "tuned": {"threads": threads, "onchip_vecs": onchip, "cluster_size": pack_size,
-                             "cluster_min_qubits": pack_min if pack_size > 1 else None},
+                   "tuned": {"threads": threads, "onchip_vecs": onchip,
+                             "packing": {1: "one CTA per instance", 2: "groups of CTAs in shared memory",
+                                         16: "clusters of 16 CTAs"}.get(pack_size, str(pack_size)),
+                             "packing_min_qubits": pack_min if pack_size > 1 else None},
                    "l2": "per-step traffic 16 B x N x k of the streamed instances (> L2 in total)",
                    "parallelism": f"replicas x{world}"},
-        "roofline": dict(hbm_roofline(hbm, t_max / args.steps, "k_batch", peaks, peak_src),
-                         note="mixed launch: instances up to the tuned on-chip size run from shared memory and add "
-                              "no HBM bytes; the per-class records in `parts` give each class against its own bound"),
+        "roofline": dict(hbm_roofline(hbm, t_max / args.steps, "k_batch + k_batch_group / k_batch_cluster",
+                                      peaks, peak_src),
+                         note="mixed graph: instances held in shared memory (one CTA, or a group of CTAs) move no "
+                              "HBM bytes per iteration; the per-class records in `parts` give each class against its "
+                              "own bound"),
         "parts": parts,
         "e2e": {"value": float(sum((1 << n) * k for n, k in zip(ns, ks))) * e2e_steps / e2e_t, "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8 * len(ns), "steps": e2e_steps},

@@ -315,37 +315,46 @@ grover_status grover_batch_create(grover_batch **out, size_t count, const int *n
  * (asynchronous).  A persistent grid takes instances from a work counter; one
  * thread block runs an instance's whole search (initial state, k iterations,
  * success probability), keeping it in shared memory when it fits the tuned
- * threshold.  Sums are exact as in grover_iterate (complex64 default). */
+ * threshold; the large instances run as grover_batch_set_packing says (by
+ * default on groups of CTAs, one cooperative launch per instance size, before
+ * the small ones).  Sums are exact as in grover_iterate (complex64 default). */
 grover_status grover_batch_run(grover_batch *b);
 
 /* Times the batch under each thread count (256, 512, 1024) and on-chip
  * threshold (32, 64, 128 KiB) of the one-CTA kernel and keeps the fastest,
  * then times the whole batch with one CTA per instance against clusters of 16
- * for the instances of at least 17, or at least 19, qubits
- * (grover_batch_set_packing, grover_batch_set_packing_min_qubits) and keeps the
- * fastest (the batch runs about 24 times); the one-CTA kernel's choice is
- * returned if the pointers are not NULL (grover_batch_get_packing gives the
- * packing).  Synchronous. */
+ * for the instances of at least 17 or 19 qubits and groups of CTAs for those
+ * of at least 15, 17 or 19 qubits (grover_batch_set_packing,
+ * grover_batch_set_packing_min_qubits) and keeps the fastest (the batch runs
+ * about 30 times); the one-CTA kernel's choice is returned if the pointers are
+ * not NULL (grover_batch_get_packing gives the packing).  Synchronous. */
 grover_status grover_batch_tune(grover_batch *b, int *threads, uint32_t *onchip_vecs);
 
-/* How instances map to the GPU: 0 or 1 (the default) runs every instance on
- * one CTA; 16 runs each instance with n >= the packing threshold (17 unless
- * set below) on one thread-block cluster of 16 CTAs -- each CTA a slice of the
- * state, in shared memory up to 200 KiB per CTA (n <= 18), else streamed
- * through L2 with one large state per cluster live; the exact partial sums of
- * an iteration meet through distributed shared memory after a hardware
- * cluster barrier -- and the rest one per CTA.  GROVER_EINVAL for other
- * values, GROVER_EUNSUPPORTED for 16 where clusters cannot run.  Rebuilds the
- * captured graph. */
+/* How instances map to the GPU (default: 2 with threshold 15 where
+ * cooperative launches run, else 1).  0 or 1: every instance on one CTA.
+ * 16: each instance with n >= the packing threshold (at least 17) on one
+ * thread-block cluster of 16 CTAs -- each CTA a slice of the state, in shared
+ * memory up to 200 KiB per CTA (n <= 18), else streamed through L2 with one
+ * large state per cluster live; the exact partial sums of an iteration meet
+ * through distributed shared memory after a hardware cluster barrier -- and
+ * the rest one per CTA.  2: each instance with n >= the threshold (at least
+ * 15) whose state fits the shared memory of at most all SMs runs on a group of
+ * G CTAs, G = ceil(state / 226 KiB) (n = 20: 37), the whole search in shared
+ * memory, the exact partial sums exchanged through global memory every
+ * iteration (bounded waits: grover_batch_success returns GROVER_ETIMEOUT if one
+ * ran out); one cooperative launch per instance size, floor(SMs / G) groups
+ * each taking its share of the instances; the rest one per CTA.  GROVER_EINVAL
+ * for other values, GROVER_EUNSUPPORTED where clusters (16) or cooperative
+ * launches (2) cannot run.  Rebuilds the captured graph. */
 grover_status grover_batch_set_packing(grover_batch *b, int cluster_size);
 
-/* Sets the packing threshold: with packing 16, instances of at least
- * min_qubits qubits (17 to 26) run on clusters.  GROVER_EINVAL outside that
- * range.  Rebuilds the captured graph. */
+/* Sets the packing threshold in qubits (15 to 26; clusters use at least 17).
+ * GROVER_EINVAL outside that range.  Rebuilds the captured graph. */
 grover_status grover_batch_set_packing_min_qubits(grover_batch *b, int min_qubits);
 
-/* The packing in use: *cluster_size 1 (one CTA per instance) or 16, and the
- * threshold in qubits (either pointer may be NULL). */
+/* The packing in use: *cluster_size 1 (one CTA per instance), 2 (groups of
+ * CTAs) or 16 (clusters), and the threshold in qubits (either pointer may be
+ * NULL). */
 grover_status grover_batch_get_packing(const grover_batch *b, int *cluster_size, int *min_qubits);
 
 /* Copies the count success probabilities sum_marked |c_x|^2 (FP64) of the last

@@ -314,7 +314,9 @@ class Batch:
 
     def set_packing(self, cluster_size: int, min_qubits: int | None = None):
         """16: clusters of 16 CTAs for instances with n >= min_qubits (17 by
-        default); 0 or 1: one CTA each."""
+        default, at least 17); 2: groups of CTAs holding the state in shared
+        memory for instances with n >= min_qubits (at least 15); 0 or 1: one
+        CTA each."""
         if min_qubits is not None:
             _check(lib().grover_batch_set_packing_min_qubits(self.handle, int(min_qubits)))
         _check(lib().grover_batch_set_packing(self.handle, int(cluster_size)))

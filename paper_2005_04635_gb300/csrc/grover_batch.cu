@@ -27,8 +27,24 @@ struct grover_batch {
     BatchClusterLaunch LC;  // large instances, one cluster each
     unsigned grid;
     int clusters;           // co-resident clusters (0: cluster packing unavailable)
-    int packing;            // 0: one CTA per instance; kBatchClusterSize: clusters for large instances
-    int pack_min_qubits;    // with packing: instances of at least this many qubits run on clusters
+    int packing;            // 0 / 1: one CTA per instance; kBatchClusterSize: clusters for the large
+                            // instances; kBatchPackGroups: groups of CTAs for the large instances
+    int pack_min_qubits;    // with packing: instances of at least this many qubits leave the one-CTA kernel
+    // groups of CTAs (packing == kBatchPackGroups): one launch per instance size
+    struct GroupClass {
+        int n;
+        unsigned groups, ctas;  // groups x CTAs per group
+        uint32_t slice_vecs;
+        size_t smem;
+        uint32_t list_off, goff_off;  // into the device glist / goff arrays
+    };
+    std::vector<GroupClass> gclasses;
+    void *group_mem;        // glist, goff, the exchange region, the status word
+    unsigned long long *group_region;
+    int *group_status;
+    int group_per_sm;       // resident group-kernel CTAs per SM (0: groups unavailable)
+    size_t glist_len;       // entries of the device glist (every class's lists)
+    std::vector<uint64_t> kk;  // iterations per instance
     uint32_t *order_dev;    // [2 * count]: small order, then large order
     std::vector<uint32_t> order;  // all instances, largest N * k first
     std::vector<int> nq;    // qubits per instance
@@ -40,6 +56,8 @@ struct grover_batch {
 };
 
 namespace {
+
+constexpr int kBatchPackGroups = 2;  // packing value of the CTA-group mode
 
 grover_status bfail(grover_batch *b, grover_status st, const char *msg, cudaError_t e = cudaSuccess) {
     char buf[512];
@@ -57,10 +75,111 @@ grover_status bfail(grover_batch *b, grover_status st, const char *msg, cudaErro
 
 // Splits the instances between the two kernels (large ones to clusters when
 // packing is on and clusters can run) and uploads both orders.
+// Instances of size n that the CTA-group kernel can hold (a group fits the GPU).
+bool group_fits(const grover_batch *b, int n) {
+    if (b->group_per_sm < 1 || n < kBatchGroupMinQubits) return false;
+    const int G = batch_group_ctas(n, kBatchGroupSmemMax);
+    return G > 0 && G <= b->sm_count;
+}
+
+// Group mode: the instances of each size n >= the threshold that a group can
+// hold, spread over floor(SMs / G) groups, each next instance (largest k first)
+// to the group with the least work so far; uploads the lists and sizes the
+// exchange region for the largest class.
+grover_status plan_groups(grover_batch *b, const std::vector<uint32_t> &large) {
+    b->gclasses.clear();
+    if (b->group_mem) {
+        cudaFree(b->group_mem);
+        b->group_mem = nullptr;
+    }
+    if (large.empty()) return GROVER_OK;
+    std::vector<uint32_t> glist, goff;
+    size_t region_words_max = 0;
+    for (int n = kBatchMaxQubits; n >= kBatchGroupMinQubits; --n) {
+        std::vector<uint32_t> cls;
+        for (uint32_t i : large)
+            if (b->nq[i] == n) cls.push_back(i);
+        if (cls.empty()) continue;
+        grover_batch::GroupClass gc;
+        gc.n = n;
+        gc.ctas = (unsigned)batch_group_ctas(n, kBatchGroupSmemMax);
+        gc.groups = (unsigned)(b->sm_count / (int)gc.ctas);
+        if (gc.groups > cls.size()) gc.groups = (unsigned)cls.size();
+        const uint64_t nvec = (1ull << n) / 2;
+        gc.slice_vecs = (uint32_t)((nvec + gc.ctas - 1) / gc.ctas);
+        gc.smem = (size_t)gc.slice_vecs * 16 + ((2 * (size_t)gc.slice_vecs + 31) / 32) * 4;
+        // longest processing time first: instances by k, largest first
+        std::stable_sort(cls.begin(), cls.end(), [&](uint32_t x, uint32_t y) { return b->kk[x] > b->kk[y]; });
+        std::vector<std::vector<uint32_t>> per(gc.groups);
+        std::vector<double> load(gc.groups, 0.0);
+        for (uint32_t i : cls) {
+            const size_t g = (size_t)(std::min_element(load.begin(), load.end()) - load.begin());
+            per[g].push_back(i);
+            load[g] += (double)b->kk[i] + 1.0;
+        }
+        gc.list_off = (uint32_t)glist.size();
+        gc.goff_off = (uint32_t)goff.size();
+        uint32_t o = 0;
+        for (unsigned g = 0; g < gc.groups; ++g) {
+            goff.push_back(o);
+            for (uint32_t i : per[g]) glist.push_back(i);
+            o += (uint32_t)per[g].size();
+        }
+        goff.push_back(o);
+        region_words_max = std::max(region_words_max, (size_t)gc.groups * batch_group_region_words((int)gc.ctas));
+        b->gclasses.push_back(gc);
+    }
+    const size_t s_list = ((glist.size() * 4) + 255) & ~size_t(255), s_goff = ((goff.size() * 4) + 255) & ~size_t(255);
+    const size_t s_region = ((region_words_max * 8) + 255) & ~size_t(255);
+    char *mem = nullptr;
+    cudaError_t e = cudaMalloc((void **)&mem, s_list + s_goff + s_region + 256);
+    if (e != cudaSuccess) return bfail(b, GROVER_ENOMEM, "device allocation of the group tables", e);
+    b->group_mem = mem;
+    b->group_region = (unsigned long long *)(mem + s_list + s_goff);
+    b->group_status = (int *)(mem + s_list + s_goff + s_region);
+    if ((e = cudaMemcpy(mem, glist.data(), glist.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(mem + s_list, goff.data(), goff.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(b->group_status, 0, sizeof(int))) != cudaSuccess)
+        return bfail(b, GROVER_ECUDA, "upload of the group tables", e);
+    return GROVER_OK;
+}
+
+BatchGroupLaunch group_launch(const grover_batch *b, const grover_batch::GroupClass &gc) {
+    const char *mem = (const char *)b->group_mem;
+    const size_t s_list = ((b->glist_len * 4) + 255) & ~size_t(255);  // glist, then goff
+    BatchGroupLaunch G;
+    G.amps = b->amps;
+    G.inst = b->L.inst;
+    G.marked = b->L.marked;
+    G.glist = (const uint32_t *)mem + gc.list_off;
+    G.goff = (const uint32_t *)(mem + s_list) + gc.goff_off;
+    G.psucc = b->L.psucc;
+    G.region = b->group_region;
+    G.region_words = batch_group_region_words((int)gc.ctas);
+    G.group_ctas = gc.ctas;
+    G.slice_vecs = gc.slice_vecs;
+    G.status = b->group_status;
+    G.wait_limit = kDefaultWaitLimit;
+    return G;
+}
+
 grover_status split(grover_batch *b) {
-    const bool use = b->packing > 1 && b->clusters > 0;
+    const bool clusters = b->packing == kBatchClusterSize && b->clusters > 0;
+    const bool groups = b->packing == kBatchPackGroups && b->group_per_sm > 0;
     std::vector<uint32_t> small, large;
-    for (uint32_t i : b->order) ((use && b->nq[i] >= b->pack_min_qubits) ? large : small).push_back(i);
+    for (uint32_t i : b->order) {
+        const int n = b->nq[i];
+        const bool big = (clusters && n >= std::max(b->pack_min_qubits, kBatchClusterMinQubits)) ||
+                         (groups && n >= b->pack_min_qubits && group_fits(b, n));
+        (big ? large : small).push_back(i);
+    }
+    if (groups) {
+        b->glist_len = large.size();
+        if (grover_status st = plan_groups(b, large)) return st;
+        large.clear();  // the group launches take them; the cluster kernel gets none
+    } else {
+        b->gclasses.clear();
+    }
     cudaError_t e = cudaSuccess;
     if (!small.empty())
         e = cudaMemcpy(b->order_dev, small.data(), small.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
@@ -86,10 +205,19 @@ grover_status rebuild(grover_batch *b) {
     cudaStream_t cs;
     if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess)
         return bfail(b, GROVER_ECUDA, "capture stream", e);
+    size_t gsmem = 0;
+    for (const auto &gc : b->gclasses) gsmem = std::max(gsmem, gc.smem);
+    if (gsmem) {
+        int per_sm = 0;
+        if ((e = prepare_batch_group(gsmem, &per_sm)) != cudaSuccess) return bfail(b, GROVER_ECUDA, "group kernel set-up", e);
+    }
     e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         // large instances first (they hold the longest runs), then the small ones
-        cudaError_t e2 = b->LC.count ? enqueue_batch_cluster(b->LC, b->clusters, cs) : cudaSuccess;
+        cudaError_t e2 = cudaSuccess;
+        for (const auto &gc : b->gclasses)
+            if (e2 == cudaSuccess) e2 = enqueue_batch_group(group_launch(b, gc), gc.groups, gc.smem, cs);
+        if (e2 == cudaSuccess && b->LC.count) e2 = enqueue_batch_cluster(b->LC, b->clusters, cs);
         if (e2 == cudaSuccess) e2 = enqueue_batch(b->L, b->grid, cs);
         e = cudaStreamEndCapture(cs, &b->graph);
         if (e2 != cudaSuccess) e = e2;
@@ -160,7 +288,14 @@ grover_status grover_batch_create(grover_batch **out, size_t count, const int *n
     if (!b) return bfail(nullptr, GROVER_ENOMEM, "host allocation of the batch");
     b->order = order;
     b->nq.resize(count);
-    for (size_t i = 0; i < count; ++i) b->nq[i] = inst[i].n;
+    b->kk.resize(count);
+    for (size_t i = 0; i < count; ++i) {
+        b->nq[i] = inst[i].n;
+        b->kk[i] = inst[i].k;
+    }
+    b->group_mem = nullptr;
+    b->gclasses.clear();
+    b->glist_len = 0;
     b->count = count;
     b->stream = (cudaStream_t)cuda_stream;
     b->amps = (float4 *)dev_amps;
@@ -203,8 +338,20 @@ grover_status grover_batch_create(grover_batch **out, size_t count, const int *n
         (void)cudaGetLastError();
         b->clusters = 0;
     }
-    b->packing = 0;  // one CTA per instance; grover_batch_tune also tries clusters
-    b->pack_min_qubits = kBatchClusterMinQubits;
+    {
+        int coop = 0, per_sm = 0;
+        b->group_per_sm = 0;
+        if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
+            prepare_batch_group(kBatchGroupSmemMax, &per_sm) == cudaSuccess)
+            b->group_per_sm = per_sm;
+        (void)cudaGetLastError();
+    }
+    // default: groups of CTAs for the instances of at least 15 qubits where
+    // cooperative launches run (measured faster than one CTA per instance for
+    // every size from 15 to 20 qubits), else one CTA per instance;
+    // grover_batch_tune also tries the other packings
+    b->packing = b->group_per_sm > 0 ? kBatchPackGroups : 0;
+    b->pack_min_qubits = b->group_per_sm > 0 ? kBatchGroupMinQubits : kBatchClusterMinQubits;
     if ((e = cudaMemcpy((void *)L.inst, inst.data(), count * sizeof(BatchInst), cudaMemcpyHostToDevice)) !=
             cudaSuccess ||
         (total_marked && (e = cudaMemcpy((void *)L.marked, marked, total_marked * sizeof(uint64_t),
@@ -278,7 +425,7 @@ grover_status grover_batch_tune(grover_batch *b, int *threads_out, uint32_t *onc
     // then whole graphs: one CTA per instance against clusters for the large ones
     b->packing = 0;
     if (grover_status st = rebuild(b)) return st;
-    if (b->clusters > 0) {
+    if (b->clusters > 0 || b->group_per_sm > 0) {
         auto time_graph = [&](float *ms) {
             return cudaGraphLaunch(b->exec, b->stream) == cudaSuccess && cudaEventRecord(e0, b->stream) == cudaSuccess &&
                    cudaGraphLaunch(b->exec, b->stream) == cudaSuccess && cudaEventRecord(e1, b->stream) == cudaSuccess &&
@@ -289,7 +436,7 @@ grover_status grover_batch_tune(grover_batch *b, int *threads_out, uint32_t *onc
         // L2), or none
         float t_best = 0.f;
         const bool ok1 = time_graph(&t_best);
-        int best_min = 0;
+        int best_min = 0, best_mode = 0;
         grover_status st = GROVER_OK;
         if (ok1) {
             static const int kMinOpts[] = {kBatchClusterMinQubits, kBatchClusterMinQubits + 2};
@@ -304,13 +451,32 @@ grover_status grover_batch_tune(grover_batch *b, int *threads_out, uint32_t *onc
                 if (st == GROVER_OK && time_graph(&t) && t < t_best) {
                     t_best = t;
                     best_min = mq;
+                    best_mode = kBatchClusterSize;
+                }
+                (void)cudaGetLastError();
+            }
+            // groups of CTAs for the instances of at least 15, 17 or 19 qubits
+            static const int kGroupMinOpts[] = {kBatchGroupMinQubits, kBatchGroupMinQubits + 2,
+                                                kBatchGroupMinQubits + 4};
+            for (int mq : kGroupMinOpts) {
+                bool any = false;
+                for (int q : b->nq) any = any || (q >= mq && group_fits(b, q));
+                if (!any) continue;
+                b->packing = kBatchPackGroups;
+                b->pack_min_qubits = mq;
+                float t = 0.f;
+                st = rebuild(b);
+                if (st == GROVER_OK && time_graph(&t) && t < t_best) {
+                    t_best = t;
+                    best_min = mq;
+                    best_mode = kBatchPackGroups;
                 }
                 (void)cudaGetLastError();
             }
         } else {
             (void)cudaGetLastError();
         }
-        b->packing = best_min ? kBatchClusterSize : 0;
+        b->packing = best_mode;
         b->pack_min_qubits = best_min ? best_min : kBatchClusterMinQubits;
         if ((st = rebuild(b)) != GROVER_OK) {
             cudaEventDestroy(e0);
@@ -327,25 +493,27 @@ grover_status grover_batch_tune(grover_batch *b, int *threads_out, uint32_t *onc
 
 grover_status grover_batch_set_packing(grover_batch *b, int cluster_size) {
     if (!b) return bfail(nullptr, GROVER_EINVAL, "batch is NULL");
-    if (cluster_size != 0 && cluster_size != 1 && cluster_size != kBatchClusterSize)
-        return bfail(b, GROVER_EINVAL, "cluster size must be 0, 1 or 16");
+    if (cluster_size != 0 && cluster_size != 1 && cluster_size != kBatchClusterSize && cluster_size != kBatchPackGroups)
+        return bfail(b, GROVER_EINVAL, "packing must be 0, 1, 2 or 16");
     if (cluster_size == kBatchClusterSize && b->clusters == 0)
         return bfail(b, GROVER_EUNSUPPORTED, "clusters of 16 CTAs cannot run on this device");
+    if (cluster_size == kBatchPackGroups && b->group_per_sm == 0)
+        return bfail(b, GROVER_EUNSUPPORTED, "the CTA-group kernel cannot run on this device");
     b->packing = cluster_size;
     return rebuild(b);
 }
 
 grover_status grover_batch_set_packing_min_qubits(grover_batch *b, int min_qubits) {
     if (!b) return bfail(nullptr, GROVER_EINVAL, "batch is NULL");
-    if (min_qubits < kBatchClusterMinQubits || min_qubits > kBatchMaxQubits)
-        return bfail(b, GROVER_EINVAL, "the packing threshold must be in [17, 26] qubits");
+    if (min_qubits < kBatchGroupMinQubits || min_qubits > kBatchMaxQubits)
+        return bfail(b, GROVER_EINVAL, "the packing threshold must be in [15, 26] qubits");
     b->pack_min_qubits = min_qubits;
     return rebuild(b);
 }
 
 grover_status grover_batch_get_packing(const grover_batch *b, int *cluster_size, int *min_qubits) {
     if (!b) return bfail(nullptr, GROVER_EINVAL, "batch is NULL");
-    if (cluster_size) *cluster_size = b->packing > 1 ? b->packing : 1;
+    if (cluster_size) *cluster_size = b->packing > 1 ? b->packing : 1;  // 1, 2 (groups) or 16
     if (min_qubits) *min_qubits = b->pack_min_qubits;
     return GROVER_OK;
 }
@@ -353,8 +521,15 @@ grover_status grover_batch_get_packing(const grover_batch *b, int *cluster_size,
 grover_status grover_batch_success(grover_batch *b, double *p_success) {
     if (!b || !p_success) return bfail(b, GROVER_EINVAL, "NULL argument");
     cudaError_t e = cudaMemcpyAsync(p_success, b->L.psucc, b->count * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+    int status = 0;
+    if (e == cudaSuccess && b->group_mem)
+        e = cudaMemcpyAsync(&status, b->group_status, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bfail(b, GROVER_ECUDA, "batch result copy", e);
+    if (status) {
+        (void)cudaMemset(b->group_status, 0, sizeof(int));
+        return bfail(b, GROVER_ETIMEOUT, "a bounded wait of a CTA group gave up; the results are undefined");
+    }
     return GROVER_OK;
 }
 
@@ -366,6 +541,7 @@ grover_status grover_batch_destroy(grover_batch *b) {
         cudaGraphDestroy(b->graph);
     }
     cudaFree(b->dev_mem);
+    if (b->group_mem) cudaFree(b->group_mem);
     delete b;
     if (e != cudaSuccess) return bfail(nullptr, GROVER_ECUDA, "grover_batch_destroy", e);
     return GROVER_OK;

@@ -222,6 +222,37 @@ struct BatchClusterLaunch {
 cudaError_t prepare_batch_cluster(int *clusters);
 cudaError_t enqueue_batch_cluster(const BatchClusterLaunch &L, int clusters, cudaStream_t st);
 
+// Large instances kept on chip by groups of CTAs (k_batch_group.cu): one
+// cooperative launch per instance size n, groups of group_ctas CTAs, each
+// running the instances glist[goff[g] .. goff[g + 1]) with exact per-iteration
+// exchanges through its part of `region` (region_words words per group, zero
+// at launch).
+constexpr int kBatchGroupThreads = 512;
+constexpr int kBatchGroupMinQubits = 15;   // smallest n a group may take
+constexpr size_t kBatchGroupSmemMax = 226 * 1024;
+struct BatchGroupLaunch {
+    float4 *amps;
+    const BatchInst *inst;
+    const uint64_t *marked;
+    const uint32_t *glist;      // instance indices, group by group
+    const uint32_t *goff;       // [groups + 1] offsets into glist
+    double *psucc;
+    unsigned long long *region; // exchange words, groups x region_words
+    size_t region_words;
+    unsigned group_ctas;
+    uint32_t slice_vecs;        // shared-memory vectors per CTA (the largest slice of this size)
+    int *status;                // 3 if a wait runs out
+    long long wait_limit;
+};
+// CTAs of one group for a 2^n-amplitude instance: the fewest whose slices
+// (plus the slice's marked bitmask) fit smem_max bytes each.
+int batch_group_ctas(int n, size_t smem_max);
+size_t batch_group_region_words(int group_ctas);
+// Sets the kernel's shared-memory limit; *per_sm = resident CTAs per SM.
+cudaError_t prepare_batch_group(size_t smem, int *per_sm);
+// Zeroes the region and launches groups x group_ctas CTAs (cooperative).
+cudaError_t enqueue_batch_group(const BatchGroupLaunch &L, unsigned groups, size_t smem, cudaStream_t st);
+
 // ---- generalised phase iterator and its adjoint (k_phase.cu), complex64 ----
 constexpr int kPhaseMaxGrid = 2048;  // CTAs of a phase-iterator launch
 constexpr uint64_t kPhaseMaxMarked = 256;
