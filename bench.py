@@ -1015,6 +1015,53 @@ def run_gate_kernels(args):
     return out
 
 
+def run_batch_classes(args):
+    """The batched workload's instance classes (n = 15-16, 17-18, 19, 20 of the
+    seeded 4096-instance batch), or with --batch-n one class of --batch-count
+    seeded instances of that size: each timed with CUDA events under each
+    packing -- one CTA per instance (tuned), groups of CTAs holding the state
+    in shared memory, clusters of 16 CTAs -- with P_success against the closed
+    form."""
+    import math
+    import torch
+    from paper_2005_04635_gb300 import binding, inputs
+    torch.cuda.set_device(0)
+    binding.lib()
+    if args.batch_n:
+        g = inputs.rng(4200 + args.batch_n)
+        n = args.batch_n
+        ms = [int(x) for x in g.integers(1, 9, args.batch_count)]
+        marks = [inputs.marked_indices(n, m, 4300 + i) for i, m in enumerate(ms)]
+        ks = [int(math.floor(0.78539816339744830962 * math.sqrt((1 << n) / m))) for m in ms]
+        classes = {f"n{n}": ([n] * len(ms), ks, marks)}
+    else:
+        ns, ks, marks = batched_instances()
+        classes = {}
+        for lo, hi in ((15, 16), (17, 18), (19, 19), (20, 20)):
+            sel = [i for i, n in enumerate(ns) if lo <= n <= hi]
+            classes[f"n{lo}-{hi}"] = ([ns[i] for i in sel], [ks[i] for i in sel], [marks[i] for i in sel])
+    stream = torch.cuda.current_stream()
+    out = {"study": "batch-classes"}
+    for name, (cn, ck, cm) in classes.items():
+        b = binding.Batch(cn, ck, cm, stream=stream)
+        b.tune()
+        rec = {"instances": len(cn), "amp_updates": float(sum((1 << n) * k for n, k in zip(cn, ck))),
+               "tuned_packing": b.packing()}
+        for label, pk, mq in (("one_cta", 0, 17), ("groups", 2, 15), ("clusters", 16, 17)):
+            if pk == 16 and max(cn) < 17:
+                continue
+            b.set_packing(pk, mq)
+            for _ in range(args.warmup):
+                b.run()
+            t = _timed_events(b.run, args.steps, stream)
+            p = b.success()
+            err = max(abs(pi - p_success_closed_form(n, len(mk), k)) for pi, n, mk, k in zip(p, cn, cm, ck))
+            rec[label] = {"ms": t * 1e3, "value": rec["amp_updates"] / t, "max_p_success_err": err}
+        b.close()
+        out[name] = rec
+    return out
+
+
 # ---- reference arm: the oracle on the host cores -----------------------------------------------------
 def run_reference(args):
     rank, world, local = dist_env()
@@ -1093,7 +1140,10 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-n28", dest="n28", action="store_false",
                     help="skip the n = 28 full-search records of the default line")
-    ap.add_argument("--study", choices=["precision", "phase", "phase-kernels", "gate-kernels"], default=None,
+    ap.add_argument("--batch-n", type=int, default=0, help="batch-classes study: one class of this size")
+    ap.add_argument("--batch-count", type=int, default=16, help="batch-classes study: instances of that class")
+    ap.add_argument("--study", choices=["precision", "phase", "phase-kernels", "gate-kernels", "batch-classes"],
+                    default=None,
                     help="run a study instead of the throughput benchmark")
     ap.add_argument("--gate-n", type=int, default=26, help="qubits of the gate-kernels study")
     ap.add_argument("--gate-iters", type=int, default=2,
@@ -1111,6 +1161,8 @@ def main(argv=None):
         out = run_phase_kernels(args)
     elif args.study == "gate-kernels":
         out = run_gate_kernels(args)
+    elif args.study == "batch-classes":
+        out = run_batch_classes(args)
     elif args.workload == "batched-4096" and args.impl != "reference":
         out = run_batched(args)
     else:
