@@ -357,6 +357,14 @@ grover_status grover_batch_set_packing_min_qubits(grover_batch *b, int min_qubit
  * NULL). */
 grover_status grover_batch_get_packing(const grover_batch *b, int *cluster_size, int *min_qubits);
 
+/* Options of the groups-of-CTAs launches: GROVER_OPT_WAIT_LIMIT (polls of a
+ * bounded wait, default 2^22) and GROVER_OPT_TEST_STALL (1: in the next runs
+ * the first CTA of the first group withholds its first partial sums, so that
+ * group's waits run out and grover_batch_success returns GROVER_ETIMEOUT; the
+ * other groups and the small instances are unaffected; 0: off).  GROVER_EINVAL
+ * for other options or values.  Rebuilds the captured graph. */
+grover_status grover_batch_set_option(grover_batch *b, grover_option opt, int64_t value);
+
 /* Copies the count success probabilities sum_marked |c_x|^2 (FP64) of the last
  * run to the HOST array p_success.  Synchronous. */
 grover_status grover_batch_success(grover_batch *b, double *p_success);

@@ -54,6 +54,7 @@ _SIGS = {
     "grover_batch_set_packing": (ctypes.c_int, [_vp, ctypes.c_int]),
     "grover_batch_set_packing_min_qubits": (ctypes.c_int, [_vp, ctypes.c_int]),
     "grover_batch_get_packing": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "grover_batch_set_option": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int64]),
     "grover_batch_success": (ctypes.c_int, [_vp, _vp]),
     "grover_batch_destroy": (ctypes.c_int, [_vp]),
     "grover_phase_forward": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_uint64, _vp]),
@@ -320,6 +321,10 @@ class Batch:
         if min_qubits is not None:
             _check(lib().grover_batch_set_packing_min_qubits(self.handle, int(min_qubits)))
         _check(lib().grover_batch_set_packing(self.handle, int(cluster_size)))
+
+    def set_option(self, opt: int, value: int):
+        """grover_batch_set_option: 2 wait limit, 3 test stall."""
+        _check(lib().grover_batch_set_option(self.handle, int(opt), int(value)))
 
     def packing(self):
         """(cluster size, threshold in qubits) in use."""

@@ -44,6 +44,8 @@ struct grover_batch {
     int *group_status;
     int group_per_sm;       // resident group-kernel CTAs per SM (0: groups unavailable)
     size_t glist_len;       // entries of the device glist (every class's lists)
+    long long wait_limit;   // polls of a bounded wait in the group kernel
+    int test_stall;         // test hook: group 0's first exchange never completes
     std::vector<uint64_t> kk;  // iterations per instance
     uint32_t *order_dev;    // [2 * count]: small order, then large order
     std::vector<uint32_t> order;  // all instances, largest N * k first
@@ -159,7 +161,8 @@ BatchGroupLaunch group_launch(const grover_batch *b, const grover_batch::GroupCl
     G.group_ctas = gc.ctas;
     G.slice_vecs = gc.slice_vecs;
     G.status = b->group_status;
-    G.wait_limit = kDefaultWaitLimit;
+    G.wait_limit = b->wait_limit;
+    G.stall = b->test_stall;
     return G;
 }
 
@@ -296,6 +299,8 @@ grover_status grover_batch_create(grover_batch **out, size_t count, const int *n
     b->group_mem = nullptr;
     b->gclasses.clear();
     b->glist_len = 0;
+    b->wait_limit = kDefaultWaitLimit;
+    b->test_stall = 0;
     b->count = count;
     b->stream = (cudaStream_t)cuda_stream;
     b->amps = (float4 *)dev_amps;
@@ -508,6 +513,23 @@ grover_status grover_batch_set_packing_min_qubits(grover_batch *b, int min_qubit
     if (min_qubits < kBatchGroupMinQubits || min_qubits > kBatchMaxQubits)
         return bfail(b, GROVER_EINVAL, "the packing threshold must be in [15, 26] qubits");
     b->pack_min_qubits = min_qubits;
+    return rebuild(b);
+}
+
+grover_status grover_batch_set_option(grover_batch *b, grover_option opt, int64_t value) {
+    if (!b) return bfail(nullptr, GROVER_EINVAL, "batch is NULL");
+    switch (opt) {
+    case GROVER_OPT_WAIT_LIMIT:
+        if (value < 1) return bfail(b, GROVER_EINVAL, "wait limit must be >= 1");
+        b->wait_limit = value;
+        break;
+    case GROVER_OPT_TEST_STALL:
+        if (value != 0 && value != 1) return bfail(b, GROVER_EINVAL, "test stall must be 0 or 1");
+        b->test_stall = (int)value;
+        break;
+    default:
+        return bfail(b, GROVER_EINVAL, "option not available for batches (wait limit and test stall are)");
+    }
     return rebuild(b);
 }
 

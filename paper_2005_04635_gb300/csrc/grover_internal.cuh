@@ -243,6 +243,7 @@ struct BatchGroupLaunch {
     uint32_t slice_vecs;        // shared-memory vectors per CTA (the largest slice of this size)
     int *status;                // 3 if a wait runs out
     long long wait_limit;
+    int stall;                  // test hook: CTA 0 of group 0 withholds its first partial sums
 };
 // CTAs of one group for a 2^n-amplitude instance: the fewest whose slices
 // (plus the slice's marked bitmask) fit smem_max bytes each.

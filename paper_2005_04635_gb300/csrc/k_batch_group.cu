@@ -177,8 +177,9 @@ __global__ void __launch_bounds__(kBatchGroupThreads, 1) k_batch_group(BatchGrou
                     const double sdv[2] = {s1, s2};
                     u128 tot[2];
                     double tsd[2];
+                    const bool withhold = L.stall && g == 0 && rank == 0 && xi == 0;  // test hook
                     const bool ok = gx_exchange<2>(v, sdv, any_side, region, s_prev, xi, G, rank, L.wait_limit,
-                                                   false, tot, tsd);
+                                                   withhold, tot, tsd);
                     if (ok) s_two = two_mu_pair(tot[0], tot[1], tsd[0], tsd[1], I.n);
                     else s_abort = 1;
                 }

@@ -127,3 +127,28 @@ def test_batch_packing_rejects_bad_size(B):
     with pytest.raises(B.GroverError) as ei:
         b.set_packing(16, 14)  # threshold below 15 qubits
     assert ei.value.status == 1
+
+
+def test_batch_group_wait_gives_up_and_recovers(B):
+    """Failure detection without a GPU fault: the test hook makes the first CTA
+    of the first group withhold its first partial sums, the group's bounded
+    waits (short limit) run out, grover_batch_success reports GROVER_ETIMEOUT,
+    and the same batch then runs correctly."""
+    ns, ks, marks = make_instances(12, 15, 17, 4, seed=41)
+    ns2, ks2, marks2 = make_instances(12, 3, 10, 4, seed=42)
+    b = B.Batch(ns + ns2, ks + ks2, marks + marks2)
+    b.set_packing(2, 15)
+    b.set_option(2, 20000)
+    b.set_option(3, 1)
+    b.run()
+    with pytest.raises(B.GroverError) as ei:
+        b.success()
+    assert ei.value.status == 4  # GROVER_ETIMEOUT
+    b.set_option(3, 0)
+    b.run()
+    p = b.success()
+    torch.cuda.synchronize()
+    all_n, all_k, all_m = ns + ns2, ks + ks2, marks + marks2
+    for i in range(len(all_n)):
+        pref = check_instance(b.state(i).cpu().numpy(), all_n[i], all_m[i], all_k[i])
+        assert abs(p[i] - pref) <= 1e-4

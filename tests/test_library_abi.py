@@ -122,6 +122,7 @@ def test_null_handles_of_the_extended_calls(lib):
     assert lib.grover_batch_set_packing(None, 16) == 1
     assert lib.grover_batch_set_packing_min_qubits(None, 19) == 1
     assert lib.grover_batch_get_packing(None, None, None) == 1
+    assert lib.grover_batch_set_option(None, 2, 1000) == 1
     assert lib.grover_batch_run(None) == 1
     assert lib.grover_batch_destroy(None) == 0
     assert lib.grover_batch_amps_needed(2, (ctypes.c_int * 2)(5, 27)) == 0  # n above 26
