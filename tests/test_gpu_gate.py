@@ -162,15 +162,16 @@ def test_gate_exact_input(B, engine, n):
     assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(x))
 
 
-@pytest.mark.parametrize("n", [26, 29])
+@pytest.mark.parametrize("n", [26, 29, 33])
 def test_gate_default_engine_exact_input(B, n):
     """The default engine at sizes where it uses the tensor cores: n = 26 (the
-    7-bit plan, all four groups on the tensor cores) and n = 29 (the 8-bit
-    plan has fewer groups: 8, 7, 7, 7, the 7-bit ones on the tensor cores, the
-    8-bit one on CUDA cores).  Same exact input and closed form (-x, then +x)
-    as test_gate_exact_input; the input is built on the device."""
+    7-bit plan, all four groups on the tensor cores), n = 29 (the 8-bit plan
+    has fewer groups: 8, 7, 7, 7, the 7-bit ones on the tensor cores, the
+    8-bit one on CUDA cores) and n = 33 (the largest complex64 state, 64 GiB:
+    7, 7, 7, 7, 5 on the tensor cores).  Same exact input and closed form (-x,
+    then +x) as test_gate_exact_input; the input is built on the device."""
     free, _ = torch.cuda.mem_get_info()
-    if free < (4 << 30) + 2 * (8 << n):
+    if free < (4 << 30) + 3 * (8 << n):
         pytest.skip("not enough free device memory")
     plan = gate_model.pass_plan(n, -1)
     assert any(tc for _lo, _kb, tc, _s, _p in plan)
