@@ -44,6 +44,16 @@ template <int E> __device__ __forceinline__ void fix_add(u128 &acc, double &side
     acc += (v ^ neg) - neg;
 }
 
+// round-toward-zero(x 2^100) of an FP32 x with |x| < 2^54 as t 2^50 + l (both
+// of the sign of x): x 2^100 = t 2^50 + r 2^100, t = trunc(x 2^50) and
+// r = x - t 2^-50 exact in FP32, so trunc(x 2^100) = t 2^50 + trunc(r 2^100);
+// |l| < 2^50.  Float-to-integer conversions replace a variable 128-bit shift.
+__host__ __device__ __forceinline__ void fix_parts(float x, long long &t, long long &l) {
+    const float tf = truncf(x * 0x1p50f);
+    t = (long long)tf;
+    l = (long long)(fmaf(tf, -0x1p-50f, x) * 0x1p100f);
+}
+
 template <int E> __device__ __forceinline__ void fix_add(u128 &acc, double &side, float x) {
     const unsigned b = __float_as_uint(x);
     const unsigned e = (b >> 23) & 0xFFu;
@@ -58,6 +68,24 @@ template <int E> __device__ __forceinline__ void fix_add(u128 &acc, double &side
     else v = sh > -24 ? (u128)(m >> (-sh)) : (u128)0;
     const u128 neg = (u128)(__int128)((int)b >> 31);
     acc += (v ^ neg) - neg;
+}
+
+// The same sum as fix_add for FP32 values |x| < 2^E, E <= 4, with the value
+// split by fix_parts (two float-to-integer conversions) instead of a variable
+// shift.  Measured on GB300: faster in the HBM-bound streaming pass (n = 33:
+// 6710 against 6654 GB/s), slower in the on-chip iterators, where the
+// conversions' latency lies on the critical path (grid iterator n = 20: 3.48
+// against 3.15 us per iteration), which therefore keep fix_add.
+template <int E> __device__ __forceinline__ void fix_add_cvt(u128 &acc, double &side, float x) {
+    static_assert(E <= 4, "fix_parts needs |x| < 2^54 and the 2^-50 part below 2^54");
+    const unsigned b = __float_as_uint(x);
+    if (((b >> 23) & 0xFFu) >= 127u + E) {
+        side = side_add(side, (double)x);
+        return;
+    }
+    long long t, l;
+    fix_parts(x, t, l);
+    acc += (u128)((__int128)t << 50) + (u128)(__int128)l;
 }
 
 __device__ __forceinline__ u128 shfl_xor_u128(u128 v, int o) {

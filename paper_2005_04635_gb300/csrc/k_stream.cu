@@ -202,8 +202,8 @@ struct AccH {  // ACC_HYBRID: FP32 pairwise group, exact above
     u128 r = 0, i = 0;
     double side_r = 0.0, side_i = 0.0;
     template <int G> __device__ __forceinline__ void add_group(const float *re, const float *im) {
-        fix_add<4>(r, side_r, pairwise<G>(re));
-        fix_add<4>(i, side_i, pairwise<G>(im));
+        fix_add_cvt<4>(r, side_r, pairwise<G>(re));
+        fix_add_cvt<4>(i, side_i, pairwise<G>(im));
     }
 };
 
