@@ -655,7 +655,7 @@ def run_batched(args):
     sm_count0 = torch.cuda.get_device_properties(0).multi_processor_count
 
     def on_chip(n):
-        return (1 << n) <= onchip_amps or (pack_size == 2 and n >= pack_min and (1 << n) * 8 <= sm_count0 * 226 * 1024)
+        return (1 << n) <= onchip_amps or (pack_size == 2 and n >= pack_min and (1 << n) * 8 <= sm_count0 * 225 * 1024)
     hbm = sum(8 * (1 << n) if on_chip(n) else 16 * (1 << n) * k + 8 * (1 << n) for n, k in zip(ns, ks))
     peaks, peak_src = measured_peaks()
     achieved = hbm * args.steps / t_max / 1e9
@@ -666,7 +666,7 @@ def run_batched(args):
     # packing chosen by the tuner), and the rest streamed through L2 / HBM
     sm_count = torch.cuda.get_device_properties(0).multi_processor_count
     sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz") or 2070.0
-    group_ok = lambda n: n >= pack_min and (1 << n) * 8 <= sm_count * 226 * 1024
+    group_ok = lambda n: n >= pack_min and (1 << n) * 8 <= sm_count * 225 * 1024
     cls_of = {}
     for i, n in enumerate(ns):
         if (1 << n) <= onchip_amps:

@@ -339,7 +339,7 @@ grover_status grover_batch_tune(grover_batch *b, int *threads, uint32_t *onchip_
  * through distributed shared memory after a hardware cluster barrier -- and
  * the rest one per CTA.  2: each instance with n >= the threshold (at least
  * 15) whose state fits the shared memory of at most all SMs runs on a group of
- * G CTAs, G = ceil(state / 226 KiB) (n = 20: 37), the whole search in shared
+ * G CTAs, G = ceil(state / 225 KiB) (n = 20: 37), the whole search in shared
  * memory, the exact partial sums exchanged through global memory every
  * iteration (bounded waits: grover_batch_success returns GROVER_ETIMEOUT if one
  * ran out); one cooperative launch per instance size, floor(SMs / G) groups

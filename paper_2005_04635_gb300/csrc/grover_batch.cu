@@ -109,7 +109,7 @@ grover_status plan_groups(grover_batch *b, const std::vector<uint32_t> &large) {
         if (gc.groups > cls.size()) gc.groups = (unsigned)cls.size();
         const uint64_t nvec = (1ull << n) / 2;
         gc.slice_vecs = (uint32_t)((nvec + gc.ctas - 1) / gc.ctas);
-        gc.smem = (size_t)gc.slice_vecs * 16 + ((2 * (size_t)gc.slice_vecs + 31) / 32) * 4;
+        gc.smem = (size_t)gc.slice_vecs * 16;
         // longest processing time first: instances by k, largest first
         std::stable_sort(cls.begin(), cls.end(), [&](uint32_t x, uint32_t y) { return b->kk[x] > b->kk[y]; });
         std::vector<std::vector<uint32_t>> per(gc.groups);

@@ -229,7 +229,7 @@ cudaError_t enqueue_batch_cluster(const BatchClusterLaunch &L, int clusters, cud
 // at launch).
 constexpr int kBatchGroupThreads = 512;
 constexpr int kBatchGroupMinQubits = 15;   // smallest n a group may take
-constexpr size_t kBatchGroupSmemMax = 226 * 1024;
+constexpr size_t kBatchGroupSmemMax = 225 * 1024;  // dynamic shared memory per CTA (227 KiB less static)
 struct BatchGroupLaunch {
     float4 *amps;
     const BatchInst *inst;
@@ -245,8 +245,8 @@ struct BatchGroupLaunch {
     long long wait_limit;
     int stall;                  // test hook: CTA 0 of group 0 withholds its first partial sums
 };
-// CTAs of one group for a 2^n-amplitude instance: the fewest whose slices
-// (plus the slice's marked bitmask) fit smem_max bytes each.
+// CTAs of one group for a 2^n-amplitude instance: the fewest whose slices fit
+// smem_max bytes each.
 int batch_group_ctas(int n, size_t smem_max);
 size_t batch_group_region_words(int group_ctas);
 // Sets the kernel's shared-memory limit; *per_sm = resident CTAs per SM.

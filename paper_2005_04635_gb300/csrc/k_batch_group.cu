@@ -2,7 +2,7 @@
 // of CTAs.
 //
 // A state of 2^n complex64 amplitudes with n >= 15 does not fit one CTA's
-// shared memory, but it fits that of G = ceil(8 * 2^n / 226 KiB) SMs (n = 20:
+// shared memory, but it fits that of G = ceil(8 * 2^n / 225 KiB) SMs (n = 20:
 // 37).  One cooperative launch per instance size n runs P = floor(SMs / G)
 // groups of G CTAs; group g runs, one after the other, the instances the host
 // assigned to it (longest processing time first).  For each instance the CTA of
@@ -67,7 +67,10 @@ __global__ void __launch_bounds__(kBatchGroupThreads, 1) k_batch_group(BatchGrou
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     extern __shared__ __align__(16) unsigned char smem[];
     float4 *sl = reinterpret_cast<float4 *>(smem);
-    uint32_t *fm = reinterpret_cast<uint32_t *>(smem + (size_t)L.slice_vecs * sizeof(float4));
+    // the marked vectors of the slice, ascending, with their amplitude bits
+    // (1: the first of the vector's two amplitudes, 2: the second)
+    __shared__ uint32_t s_mv[kBatchMaxMarked], s_mf[kBatchMaxMarked];
+    __shared__ uint32_t s_mcnt;
     __shared__ unsigned long long wint[kBgWarps][4];
     __shared__ double wside[kBgWarps][2];
     __shared__ unsigned long long s_prev[2][GxLayout<2>::W];
@@ -88,17 +91,27 @@ __global__ void __launch_bounds__(kBatchGroupThreads, 1) k_batch_group(BatchGrou
         const uint64_t per = (nvec + G - 1) / G;  // <= L.slice_vecs (host)
         const uint64_t start = (uint64_t)rank * per;
         const uint32_t nv = start >= nvec ? 0u : (uint32_t)(nvec - start < per ? nvec - start : per);
-        const uint32_t nwords = (uint32_t)((2 * per + 31) / 32);
         const float a0 = (float)(1.0 / sqrt((double)(1ull << I.n)));  // IEEE sqrt and division
         for (uint32_t j = tid; j < nv; j += kBatchGroupThreads) sl[j] = make_float4(a0, 0.f, a0, 0.f);
-        for (uint32_t w = tid; w < nwords; w += kBatchGroupThreads) fm[w] = 0u;
-        __syncthreads();
         const uint64_t e0 = 2 * start;  // first amplitude of the slice
-        for (uint32_t i = tid; i < I.m; i += kBatchGroupThreads) {
-            const uint64_t x = L.marked[I.mark_off + i];
-            if (x >= e0 && x < e0 + 2ull * nv) atomicOr(fm + ((x - e0) >> 5), 1u << (uint32_t)((x - e0) & 31));
+        if (tid == 0) {
+            // the instance's list is sorted and unique: one pass
+            uint32_t c = 0;
+            for (uint32_t i = 0; i < I.m; ++i) {
+                const uint64_t x = L.marked[I.mark_off + i];
+                if (x < e0 || x >= e0 + 2ull * nv) continue;
+                const uint32_t j = (uint32_t)((x - e0) >> 1), bit = 1u << (uint32_t)((x - e0) & 1);
+                if (c && s_mv[c - 1] == j) s_mf[c - 1] |= bit;
+                else {
+                    s_mv[c] = j;
+                    s_mf[c] = bit;
+                    ++c;
+                }
+            }
+            s_mcnt = c;
         }
         __syncthreads();
+        const uint32_t mcnt = s_mcnt;
 
         for (long long t = -1; t < (long long)I.k; ++t) {
             const bool upd = t >= 0;
@@ -112,6 +125,11 @@ __global__ void __launch_bounds__(kBatchGroupThreads, 1) k_batch_group(BatchGrou
             }
             u128 ar = 0, ai = 0;
             double sr = 0.0, si = 0.0;
+            // a thread visits its vectors in increasing order: a cursor into the
+            // marked vectors finds the rare ones, the others take no flips
+            uint32_t cur = 0;
+            while (cur < mcnt && s_mv[cur] < (uint32_t)tid) ++cur;
+            uint32_t nextj = cur < mcnt ? s_mv[cur] : 0xFFFFFFFFu;
             for (uint32_t j0 = tid; j0 < nv; j0 += kBgU * kBatchGroupThreads) {
                 float gr[2 * kBgU], gi[2 * kBgU];
 #pragma unroll
@@ -122,20 +140,37 @@ __global__ void __launch_bounds__(kBatchGroupThreads, 1) k_batch_group(BatchGrou
                         continue;
                     }
                     float4 c = sl[j];
-                    const uint32_t e = 2 * j;
-                    const uint32_t f = (fm[e >> 5] >> (e & 31)) & 3u;
-                    const uint32_t f0 = f & 1u, f1 = f >> 1;
-                    if (upd) {
-                        c.x = (two_re - bg_flip(c.x, f0)) + lo_re;
-                        c.y = (two_im - bg_flip(c.y, f0)) + lo_im;
-                        c.z = (two_re - bg_flip(c.z, f1)) + lo_re;
-                        c.w = (two_im - bg_flip(c.w, f1)) + lo_im;
-                        sl[j] = c;
+                    while (nextj < j) {  // marked vectors of other threads
+                        ++cur;
+                        nextj = cur < mcnt ? s_mv[cur] : 0xFFFFFFFFu;
                     }
-                    gr[2 * u] = bg_flip(c.x, f0);
-                    gi[2 * u] = bg_flip(c.y, f0);
-                    gr[2 * u + 1] = bg_flip(c.z, f1);
-                    gi[2 * u + 1] = bg_flip(c.w, f1);
+                    if (j != nextj) {
+                        if (upd) {
+                            c.x = (two_re - c.x) + lo_re;
+                            c.y = (two_im - c.y) + lo_im;
+                            c.z = (two_re - c.z) + lo_re;
+                            c.w = (two_im - c.w) + lo_im;
+                            sl[j] = c;
+                        }
+                        gr[2 * u] = c.x;
+                        gi[2 * u] = c.y;
+                        gr[2 * u + 1] = c.z;
+                        gi[2 * u + 1] = c.w;
+                    } else {
+                        const uint32_t f = s_mf[cur];
+                        const uint32_t f0 = f & 1u, f1 = f >> 1;
+                        if (upd) {
+                            c.x = (two_re - bg_flip(c.x, f0)) + lo_re;
+                            c.y = (two_im - bg_flip(c.y, f0)) + lo_im;
+                            c.z = (two_re - bg_flip(c.z, f1)) + lo_re;
+                            c.w = (two_im - bg_flip(c.w, f1)) + lo_im;
+                            sl[j] = c;
+                        }
+                        gr[2 * u] = bg_flip(c.x, f0);
+                        gi[2 * u] = bg_flip(c.y, f0);
+                        gr[2 * u + 1] = bg_flip(c.z, f1);
+                        gi[2 * u + 1] = bg_flip(c.w, f1);
+                    }
                 }
                 fix_add<4>(ar, sr, bg_pairwise<2 * kBgU>(gr));
                 fix_add<4>(ai, si, bg_pairwise<2 * kBgU>(gi));
@@ -227,7 +262,7 @@ int batch_group_ctas(int n, size_t smem_max) {
     const uint64_t nvec = (1ull << n) / 2;
     for (uint64_t G = 1; G <= 1024; ++G) {
         const uint64_t per = (nvec + G - 1) / G;
-        if (per * sizeof(float4) + ((2 * per + 31) / 32) * sizeof(uint32_t) <= smem_max) return (int)G;
+        if (per * sizeof(float4) <= smem_max) return (int)G;
     }
     return 0;
 }
