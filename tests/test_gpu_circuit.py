@@ -6,7 +6,8 @@ Tolerance: X gates and the multi-controlled Z are exact; each Hadamard pass
 rounds a + b (or a - b) and the product with the rounded 1/sqrt(2), and the
 rounded scale itself is off by at most one unit: an error vector of norm at
 most 4 u per Hadamard pass for a unit-norm state, and unitary gates do not
-amplify it.  k iterations hold 2 n k Hadamard passes: max error <= 8 n k u.
+amplify it.  k iterations hold 2 n k Hadamard passes: the error vector has
+norm <= 8 n k u ||psi|| (checked as a norm).
 """
 from __future__ import annotations
 
@@ -50,7 +51,7 @@ def test_circuit_matches_oracle(B, dtype, n, m, k):
     assert gates == ref_gates
     zeros = sum(n - bin(int(x)).count("1") for x in marked)
     assert passes == k * (2 * zeros + 4 * n)
-    assert np.max(np.abs(to_np(st) - ref)) <= 8 * n * k * U[dtype] + 1e-300
+    assert np.linalg.norm(to_np(st) - ref) <= 8 * n * k * U[dtype] * np.linalg.norm(ref) + 1e-300
 
 
 def test_circuit_equals_operator_path_uniform(B):
