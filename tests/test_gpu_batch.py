@@ -7,6 +7,7 @@ from __future__ import annotations
 import numpy as np
 import pytest
 
+import c64_bounds
 import oracle
 from paper_2005_04635_gb300 import inputs
 
@@ -44,9 +45,10 @@ def check_instance(got, n, mk, k):
     mask[np.asarray(mk, dtype=np.int64)] = True
     am, au = oracle.closed_form_uniform(n, m, k)
     # the error vector of k complex64 iterations from the rounded uniform start
-    # has norm <= (3k + 1) 2^-24; the group check makes the marked (unmarked)
-    # values one number, so each is within that bound over sqrt(M) (sqrt(N - M))
-    e = (3 * k + 1) * 2.0 ** -24
+    # has norm <= c64_bounds.norm_bound(k); the group check makes the marked
+    # (unmarked) values one number, so each is within that bound over sqrt(M)
+    # (sqrt(N - M))
+    e = c64_bounds.norm_bound(k)
     for grp, ref in ((got[mask], am), (got[~mask], au)):
         if grp.size:
             assert np.all(grp == grp[0]), (n, m, k)

@@ -6,15 +6,15 @@ The whole state is checked on the device (the group invariant: every unmarked
 amplitude equals one value, every marked one another), then the two values are
 compared with the closed form one by one.
 
-complex64 bound: the FP32 start 1/sqrt(N) is off by an error vector of norm
-<= 2^-24, and each iteration adds one of norm <= 3 * 2^-24 (one FP32 rounding
-per stored amplitude, norm <= 2^-24, plus the FP32 rounding of 2 mu shared by
-all N amplitudes, norm <= sqrt(N) * 2^-24 * 2|mu| <= 2 * 2^-24); the iteration
-is unitary, so after k iterations ||error||_2 <= (3k + 1) * 2^-24.  Once the
-group check has shown that the N - M unmarked amplitudes are one value v_u
-(and the M marked ones one value v_m), the error vector holds N - M copies of
-v_u - a_u and M copies of v_m - a_m, so
-  |v_u - a_u| <= (3k + 1) 2^-24 / sqrt(N - M),  |v_m - a_m| <= (3k + 1) 2^-24 / sqrt(M).
+complex64 bound (c64_bounds, u = 2^-24): the FP32 start 1/sqrt(N) is off by
+an error vector of norm <= u, and each iteration adds one of norm
+<= (8u + 64u^2) times the state's norm (the FP32 pairwise tile sums of the
+mean, about 6u, and two roundings per stored amplitude, 2u); the iteration is
+unitary, so after k iterations ||error||_2 <= E = (1 + 8u + 64u^2)^k (1 + u) - 1.
+Once the group check has shown that the N - M unmarked amplitudes are one
+value v_u (and the M marked ones one value v_m), the error vector holds N - M
+copies of v_u - a_u and M copies of v_m - a_m, so
+  |v_u - a_u| <= E / sqrt(N - M),  |v_m - a_m| <= E / sqrt(M).
 complex128: the same argument with u = 2^-53 gives far less than the 1e-11
 the FP64 tolerance asks for.  P_success must be within 1e-4 of the FP64 value
 (complex64).
@@ -24,6 +24,7 @@ from __future__ import annotations
 import numpy as np
 import pytest
 
+import c64_bounds
 import oracle
 from paper_2005_04635_gb300 import inputs
 
@@ -42,11 +43,9 @@ def B():
 
 def group_tolerances(dtype, n, m, k):
     """Per-element bounds on the marked and the unmarked value (module docstring)."""
-    N = 1 << n
     if dtype == "c128":
         return 1e-11, 1e-11
-    e = (3 * k + 1) * 2.0 ** -24
-    return e / m ** 0.5, e / (N - m) ** 0.5
+    return c64_bounds.group_bounds(n, m, k)
 
 
 def run_and_check(B, n, m, dtype, k, seed):

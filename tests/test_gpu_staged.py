@@ -11,6 +11,7 @@ from __future__ import annotations
 import numpy as np
 import pytest
 
+import c64_bounds
 import oracle
 from paper_2005_04635_gb300 import inputs
 
@@ -75,8 +76,8 @@ def test_staged_matches_oracle(B):
     psi0 = inputs.gaussian_state(n, seed=921).astype(np.complex64)
     got, _, _ = run(B, n, "c64", B.Marked(n, marked), k, staged=1, psi0=psi0)
     ref = oracle.grover_operator(psi0.astype(np.complex128), n, marked, k)
-    # error vector of k complex64 iterations from the stored start: norm <= 3 k u ||psi||
-    assert np.linalg.norm(got.astype(np.complex128) - ref) <= 3 * k * 2.0 ** -24 * np.linalg.norm(ref) + 1e-12
+    # error vector of k complex64 iterations from the stored start (c64_bounds)
+    assert np.linalg.norm(got.astype(np.complex128) - ref) <= c64_bounds.norm_bound(k, np.linalg.norm(ref))
 
 
 def test_staged_default_above_l2(B):
@@ -89,11 +90,12 @@ def test_staged_default_above_l2(B):
     a0, _, _ = run(B, n, "c64", mk, k, staged=0)
     assert np.array_equal(a1, a0)
     am, au = oracle.closed_form_uniform(n, m, k)
-    # one marked value: the error-vector norm bound (3k + 1) u over sqrt(M)
-    assert abs(complex(a1[int(marked[0])]) - am) <= (3 * k + 1) * 2.0 ** -24 / np.sqrt(m)
+    # one marked value: the error-vector norm bound over sqrt(M) (c64_bounds)
+    tol_m, tol_u = c64_bounds.group_bounds(n, m, k)
+    assert abs(complex(a1[int(marked[0])]) - am) <= tol_m
     other = 0 if int(marked[0]) != 0 else 1
     assert np.all(np.delete(a1, marked.astype(np.int64)) == a1[other])  # the unmarked values are one number
-    assert abs(complex(a1[other]) - au) <= (3 * k + 1) * 2.0 ** -24 / np.sqrt((1 << n) - m)
+    assert abs(complex(a1[other]) - au) <= tol_u
 
 
 def test_staged_wait_runs_out(B):
