@@ -154,3 +154,29 @@ def test_batch_group_wait_gives_up_and_recovers(B):
     for i in range(len(all_n)):
         pref = check_instance(b.state(i).cpu().numpy(), all_n[i], all_m[i], all_k[i])
         assert abs(p[i] - pref) <= 1e-4
+
+
+def test_batch_group_edge_cases(B):
+    """Groups of CTAs (n = 15..20) on the cases their loop treats apart: k = 0
+    (the uniform start, written back after the first exchange), k = 1 and 2,
+    random k, a size with a single instance, the marked amplitude in the last
+    slot of the last CTA's slice; against the closed form, deterministic."""
+    ns, ks, marks = make_instances(30, 15, 20, 8, seed=51, kmode="random")
+    extra_n = [15, 15, 16, 20, 19]
+    ns += extra_n
+    ks += [0, 1, 2, 1, 0]
+    marks += [inputs.marked_indices(n, 3, 520 + i) for i, n in enumerate(extra_n)]
+    ns += [18]
+    ks += [oracle.optimal_iterations(18, 1)]
+    marks += [np.array([(1 << 18) - 1], dtype=np.uint64)]
+    b = B.Batch(ns, ks, marks)
+    b.set_packing(2, 15)
+    b.run()
+    p = b.success()
+    torch.cuda.synchronize()
+    for i in range(len(ns)):
+        pref = check_instance(b.state(i).cpu().numpy(), ns[i], marks[i], ks[i])
+        assert abs(p[i] - pref) <= 1e-4
+    s1 = b.amps.cpu().numpy().copy()
+    b.run()
+    assert np.array_equal(b.success(), p) and np.array_equal(b.amps.cpu().numpy(), s1)
