@@ -802,9 +802,10 @@ def run_precision_study(args):
     return {"study": "precision", "workload": f"n={n}, M={m} (seed {seed}), {k} iterations; complex Gaussian "
             f"start (seed {seed + 1}) as specified, and the uniform start for contrast",
             "p_success_fp64": {"gaussian": p_ref, "uniform": m * a_m * a_m},
-            # worst-case 2-norm of the complex64 error vector (default accumulation):
-            # per iteration 8u + 64u^2 (FP32 pairwise tile sums of the mean, two
-            # roundings per stored amplitude), u = 2^-24, plus u for the start
+            # worst-case 2-norm of the complex64 error vector (default accumulation,
+            # the streaming pass these runs take): per iteration 8u + 64u^2 (FP32
+            # pairwise 8-amplitude tile sums of the mean, two roundings per stored
+            # amplitude), u = 2^-24, plus u for the start
             "bound_error_norm_c64_default": (1 + 8 * 2.0 ** -24 + 64 * 2.0 ** -48) ** k * (1 + 2.0 ** -24) - 1,
             "rows": rows}
 

@@ -60,6 +60,8 @@ typedef enum { GROVER_C64 = 0, GROVER_C128 = 1 } grover_dtype;
  * mode combines per-block partial sums in a fixed order, so a result is
  * bitwise reproducible run to run.
  *   GROVER_ACC_DEFAULT: complex64: each thread's 8 amplitudes of a load group
+ *                       (16 in the on-chip grid iterator from 6 vectors per
+ *                       thread, n >= 20, and in the batches' groups of CTAs)
  *                       summed pairwise in FP32 (exact for equal values), each
  *                       such group sum added exactly as a fixed-point integer
  *                       with 100 fractional bits (group sums of magnitude 16

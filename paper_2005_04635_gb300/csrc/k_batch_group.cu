@@ -11,8 +11,8 @@
 // Algorithm "n-qubit Oracle" then Algorithm "n-qubit Inversion about Mean", k_i
 // times -- and writes them to the batch buffer once.  Per iteration the CTA
 // updates its slice, c <- 2 mu - O c, adds O c_new into exact 128-bit
-// fixed-point sums (FP32 pairwise sums of 8-amplitude groups, as everywhere
-// else), reduces them in integers and exchanges them with the other G - 1 CTAs
+// fixed-point sums (FP32 pairwise sums of 16-amplitude groups), reduces them
+// in integers and exchanges them with the other G - 1 CTAs
 // of its group through global memory (grid_exchange.cuh: limb sums and arrival
 // counts in shared words, bounded polls), so every CTA of the group obtains the
 // bitwise identical next mean; 2 mu becomes a float pair with integer
@@ -28,7 +28,10 @@ namespace grv {
 namespace {
 
 constexpr int kBgWarps = kBatchGroupThreads / 32;
-constexpr int kBgU = 4;  // vectors per thread per summation group (8 amplitudes)
+// vectors per thread per summation group: one FP32 pairwise sum of 16
+// amplitudes per exact fixed-point add (against 8: half the adds, 8 % faster
+// over the batch on GB300)
+constexpr int kBgU = 8;
 
 __device__ __forceinline__ float bg_flip(float x, uint32_t f) { return __uint_as_float(__float_as_uint(x) ^ (f << 31)); }
 

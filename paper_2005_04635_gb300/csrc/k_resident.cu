@@ -11,7 +11,8 @@
 //   1. every thread updates its amplitudes in shared memory,
 //        c <- 2 mu - O c,
 //      and adds O c_new into a 128-bit fixed-point sum (exact: 100 fractional
-//      bits; complex64 adds the FP32 pairwise sum of each 8-amplitude group);
+//      bits; complex64 adds the FP32 pairwise sum of each 8-amplitude group,
+//      16 in the grid iterator's wide slices);
 //   2. the CTA reduces its threads' sums exactly (integer shuffles) into a
 //      partial in its own shared memory;
 //   3. a hardware cluster barrier (release / acquire), then every CTA reads
@@ -302,11 +303,17 @@ static_assert(kRgBytes >= GxLayout<2>::kAccBytes + GxLayout<2>::side_bytes(kRgMa
 constexpr int kRgThreads = 512;
 constexpr int kRgWarps = kRgThreads / 32;
 
-template <class T>
+// U vectors per thread per summation group: complex64 slices of at least
+// kRgWideVecs vectors take U = 8, one FP32 pairwise sum of 16 amplitudes per
+// exact fixed-point add (half the adds: 7-11 % faster per iteration at
+// n = 20-22 on GB300), smaller slices U = 4 (8 amplitudes), where threads hold
+// too few vectors to fill a group of 16.
+constexpr uint32_t kRgWideVecs = 6 * kRgThreads;
+
+template <class T, int U>
 __global__ void __launch_bounds__(kRgThreads, 1) k_resident_grid(ResGridArgs a) {
     using V = typename Vec<T>::V;
     constexpr int APV = Vec<T>::APV;
-    constexpr int U = 4;
     const unsigned rank = blockIdx.x, G = gridDim.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
@@ -468,7 +475,9 @@ __global__ void __launch_bounds__(kRgThreads, 1) k_resident_grid(ResGridArgs a) 
 }
 
 template <class T> cudaError_t launch_grid_t(const ResGridArgs &a, unsigned G, size_t smem, cudaStream_t st) {
-    auto kern = k_resident_grid<T>;
+    void (*kern)(ResGridArgs) = k_resident_grid<T, 4>;
+    if constexpr (Vec<T>::APV == 2)
+        if (a.slice_vecs >= kRgWideVecs) kern = k_resident_grid<T, 8>;
     cudaError_t e;
     if ((e = raise_smem_limit(kern, smem)) != cudaSuccess) return e;
     int per_sm = 0;

@@ -4,22 +4,25 @@ method itself).
 
 One iteration from a stored complex64 state c, u = 2^-24:
   * y = O c is exact (sign flips).
-  * The sum S = sum_i y_i: each thread adds the 8 amplitudes of a tile
-    pairwise in FP32 (three levels, so the tile sum is within
-    gamma_3 * sum_tile |y_i| of exact, gamma_3 = 3u / (1 - 3u), for the real
-    and the imaginary part alike and hence in modulus), and the tile sums are
-    added exactly as fixed point (truncation below 2^-100 per tile).  So
-    |S_hat - S| <= gamma_3 sum_i |y_i| <= gamma_3 sqrt(N) ||c||
+  * The sum S = sum_i y_i: each thread adds the amplitudes of a tile pairwise
+    in FP32 -- 8 per tile in the streaming pass, the cluster iterator and the
+    one-CTA batches, 16 in the groups of CTAs and in the grid iterator's wide
+    slices -- so the tile sum is within gamma_4 * sum_tile |y_i| of exact
+    (at most four levels, gamma_j = j u / (1 - j u)), for the real and the
+    imaginary part alike and hence in modulus, and the tile sums are added
+    exactly as fixed point (truncation below 2^-100 per tile).  So
+    |S_hat - S| <= gamma_4 sum_i |y_i| <= gamma_4 sqrt(N) ||c||
     (Cauchy-Schwarz).  2 mu = 2 S / N reaches the update as a float pair
     hi + lo within 2^-46 |2 mu|.  Every amplitude therefore sees 2 mu off by at
-    most (2 gamma_3 + 2^-45) ||c|| / sqrt(N): an error vector of norm
-    <= (2 gamma_3 + 2^-45) ||c||.
+    most (2 gamma_4 + 2^-45) ||c|| / sqrt(N): an error vector of norm
+    <= (2 gamma_4 + 2^-45) ||c||.
   * The update c'_i = fl(fl(hi - y_i) + lo) rounds twice per stored amplitude
     (relative u each, real and imaginary parts alike): an error vector of norm
     <= 2u (1 + 8u) ||c||.
-  * Per iteration: rho = 2 gamma_3 + 2^-45 + 2u (1 + 8u) <= 8u + 64u^2 times
-    the norm of the state that enters it.  With every amplitude summed exactly
-    (GROVER_ACC_EXACT) the first term goes: rho <= 2u + 32u^2.
+  * Per iteration: rho = 2 gamma_4 + 2^-45 + 2u (1 + 8u) <= 10u + 64u^2 times
+    the norm of the state that enters it (8u + 64u^2 where every tile has 8
+    amplitudes).  With every amplitude summed exactly (GROVER_ACC_EXACT) the
+    first term goes: rho <= 2u + 32u^2.
 The exact iteration is unitary, so the error e_t after t iterations obeys
 e_{t+1} <= e_t + rho (||psi|| + e_t): e_k <= ((1 + rho)^k (1 + e_0) - 1) ||psi||,
 with e_0 <= u ||psi|| for a start rounded to complex64.
@@ -34,14 +37,15 @@ from __future__ import annotations
 import math
 
 U = 2.0 ** -24
-RHO = {"default": 8 * U + 64 * U * U, "exact": 2 * U + 32 * U * U}
+RHO = {"default": 10 * U + 64 * U * U, "tile8": 8 * U + 64 * U * U, "exact": 2 * U + 32 * U * U}
 
 
 def rho_fp64(n):
-    """GROVER_ACC_FP64: the default's tile sums, then FP64 running sums and an
-    FP64 tree, no chain of which is longer than the N / 8 tile sums: relative
-    error <= 2^(n - 3) 2^-53 (1 + 4u) on sum |tile sums|, doubled in 2 mu."""
-    return RHO["default"] + 2.0 ** (n - 55)
+    """GROVER_ACC_FP64 (streaming pass, 8-amplitude tiles): the tile sums, then
+    FP64 running sums and an FP64 tree, no chain of which is longer than the
+    N / 8 tile sums: relative error <= 2^(n - 3) 2^-53 (1 + 4u) on
+    sum |tile sums|, doubled in 2 mu."""
+    return RHO["tile8"] + 2.0 ** (n - 55)
 
 
 def norm_bound(k, norm=1.0, rho=RHO["default"], start=U):

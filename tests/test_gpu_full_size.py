@@ -8,9 +8,9 @@ compared with the closed form one by one.
 
 complex64 bound (c64_bounds, u = 2^-24): the FP32 start 1/sqrt(N) is off by
 an error vector of norm <= u, and each iteration adds one of norm
-<= (8u + 64u^2) times the state's norm (the FP32 pairwise tile sums of the
-mean, about 6u, and two roundings per stored amplitude, 2u); the iteration is
-unitary, so after k iterations ||error||_2 <= E = (1 + 8u + 64u^2)^k (1 + u) - 1.
+<= (10u + 64u^2) times the state's norm (the FP32 pairwise tile sums of the
+mean, at most 8u, and two roundings per stored amplitude, 2u); the iteration
+is unitary, so after k iterations ||error||_2 <= E = (1 + 10u + 64u^2)^k (1 + u) - 1.
 Once the group check has shown that the N - M unmarked amplitudes are one
 value v_u (and the M marked ones one value v_m), the error vector holds N - M
 copies of v_u - a_u and M copies of v_m - a_m, so

@@ -4,11 +4,12 @@ Tolerances
   * complex128: max |gpu - oracle| <= 1e-11 after the full optimal run, and
     |1 - norm| <= 1e-12; top-m / argmax indices bit-exact.
   * complex64 (default accumulation): the worst-case bound of c64_bounds
-    (u = 2^-24): per iteration the FP32 pairwise tile sums put an error vector
-    of norm <= 2 gamma_3 ||c|| ~ 6u ||c|| into 2 mu and the update
-    c <- (2mu_hi - O c) + 2mu_lo rounds twice per stored amplitude (2u ||c||);
-    the iteration is unitary, so after k iterations the error vector has norm
-    <= ((1 + 8u + 64u^2)^k (1 + u) - 1) ||c|| ~ (8k + 1) u ||c||.  The tests
+    (u = 2^-24): per iteration the FP32 pairwise tile sums (8 or 16
+    amplitudes) put an error vector of norm <= 2 gamma_4 ||c|| ~ 8u ||c|| into
+    2 mu and the update c <- (2mu_hi - O c) + 2mu_lo rounds twice per stored
+    amplitude (2u ||c||); the iteration is unitary, so after k iterations the
+    error vector has norm <= ((1 + 10u + 64u^2)^k (1 + u) - 1) ||c||
+    ~ (10k + 1) u ||c||.  The tests
     check that 2-norm; where every unmarked (marked) amplitude is one value,
     that value is within the bound over sqrt(N - M) (sqrt(M)).  The plain and
     compensated FP32 running sums have no useful worst-case bound at these
