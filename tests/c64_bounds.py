@@ -27,6 +27,20 @@ The exact iteration is unitary, so the error e_t after t iterations obeys
 e_{t+1} <= e_t + rho (||psi|| + e_t): e_k <= ((1 + rho)^k (1 + e_0) - 1) ||psi||,
 with e_0 <= u ||psi|| for a start rounded to complex64.
 
+The generalised phase iterator D(vphi) O(phi) (one pass on a stored state c):
+  * marked amplitudes take the FP32 phase factor (within u of e^{i phi}) times
+    c_x, a complex product within sqrt(5) u |c_x| of exact (Brent, Percival
+    and Zimmermann's bound; 2u with fused multiply-adds): (1 + sqrt(5)) u
+    |c_x| + O(u^2) in all;
+  * kappa = (1 - e^{i vphi}) <O c> comes from 8-amplitude FP32 tile sums added
+    exactly (the marked correction in FP64), and |1 - e^{i vphi}| <= 2, so
+    kappa's error, met by all N amplitudes, is an error vector of norm
+    <= 2 gamma_3 ||c||; its float pair adds 2^-45 ||c||;
+  * c - kappa_hi - kappa_lo rounds twice: 2u ||c'||.
+  rho_phase <= (1 + sqrt(5) + 6 + 2) u + O(u^2) <= 12u + 64u^2.  The backward
+  sweep applies the same operations (subtraction, then rotation) to the state
+  and to the adjoint, each within the same rho per pass.
+
 Where the state is known to hold one value on the M marked and one on the
 N - M unmarked amplitudes (the bitwise group check of a uniform start), the
 error vector holds M copies of one difference and N - M copies of another, so
@@ -37,7 +51,8 @@ from __future__ import annotations
 import math
 
 U = 2.0 ** -24
-RHO = {"default": 10 * U + 64 * U * U, "tile8": 8 * U + 64 * U * U, "exact": 2 * U + 32 * U * U}
+RHO = {"default": 10 * U + 64 * U * U, "tile8": 8 * U + 64 * U * U, "exact": 2 * U + 32 * U * U,
+       "phase": 12 * U + 64 * U * U}
 
 
 def rho_fp64(n):
@@ -59,3 +74,17 @@ def group_bounds(n, m, k, rho=RHO["default"]):
     of norm 1: the norm bound over sqrt(M) and over sqrt(N - M)."""
     e = norm_bound(k, 1.0, rho)
     return e / math.sqrt(m), e / math.sqrt((1 << n) - m)
+
+
+def p_bound(P, E):
+    """|P_hat - P| for P = sum over marked |c_x|^2 when the state's error vector
+    has norm <= E: sqrt(P_hat) is within E of sqrt(P) (triangle inequality on
+    the marked part), so |P_hat - P| <= 2 sqrt(P) E + E^2."""
+    return 2.0 * math.sqrt(P) * E + E * E
+
+
+def loss_bound(P, E):
+    """|log P_hat - log P| <= |dP| / (P - |dP|) (mean value theorem), for the
+    loss -log P."""
+    dP = p_bound(P, E)
+    return dP / (P - dP) if dP < P else math.inf
