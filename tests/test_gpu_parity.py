@@ -470,11 +470,12 @@ def test_resident_grid_full_run_uniform(B, dtype, n, m):
     assert abs(outs[0][other] - a_u) <= tol_u
 
 
-def test_resident_grid_wait_runs_out(B):
+@pytest.mark.parametrize("n", [18, 21])
+def test_resident_grid_wait_runs_out(B, n):
     """Failure detection without a GPU fault: CTA 0 withholds its first partial
     (test hook), every CTA's bounded wait runs out, the kernel returns and
-    grover_sync reports GROVER_ETIMEOUT; the handle stays usable."""
-    n = 18
+    grover_sync reports GROVER_ETIMEOUT; the handle stays usable (n = 21: the
+    kernel instance with 16-amplitude summation groups)."""
     marked = inputs.marked_indices(n, 2, seed=190)
     st = B.State(n, "c64")
     mk = B.Marked(n, marked)
@@ -496,7 +497,7 @@ def test_resident_grid_wait_runs_out(B):
 
 
 # ---- amplitudes outside the fixed-point window ----------------------------------------------
-@pytest.mark.parametrize("path,n", [("pass", 14), ("cluster", 12), ("grid", 18)])
+@pytest.mark.parametrize("path,n", [("pass", 14), ("cluster", 12), ("grid", 18), ("grid", 21)])
 def test_out_of_window_amplitudes(B, path, n):
     """A state scaled by 64 (amplitudes above the 16 of the exact fixed-point
     window) takes the FP64 side sums in every reduction; the iterator is linear,
