@@ -573,25 +573,23 @@ cudaError_t launch_pdl(void (*kern)(PhaseArgs), unsigned grid, cudaStream_t st, 
 
 }  // namespace
 
+// The resident CTAs per SM are queried at every launch (for the current
+// device), not cached in the process.
 cudaError_t launch_phase_fwd(const PhaseArgs &a, bool update, bool stream, cudaStream_t st, int sm_count) {
-    static const int occ[4] = {occupancy(k_phase_fwd<false, false>), occupancy(k_phase_fwd<false, true>),
-                               occupancy(k_phase_fwd<true, false>), occupancy(k_phase_fwd<true, true>)};
     void (*kern[4])(PhaseArgs) = {k_phase_fwd<false, false>, k_phase_fwd<false, true>, k_phase_fwd<true, false>,
                                   k_phase_fwd<true, true>};
     const int w = (update ? 2 : 0) + (stream ? 1 : 0);
-    return launch_pdl(kern[w], phase_grid(occ[w], a.nvec, sm_count), st, a);
+    return launch_pdl(kern[w], phase_grid(occupancy(kern[w]), a.nvec, sm_count), st, a);
 }
 
 cudaError_t launch_phase_bwd(const PhaseArgs &a, bool stream, cudaStream_t st, int sm_count) {
-    static const int occ[2] = {occupancy(k_phase_bwd<false>), occupancy(k_phase_bwd<true>)};
     void (*kern[2])(PhaseArgs) = {k_phase_bwd<false>, k_phase_bwd<true>};
-    return launch_pdl(kern[stream], phase_grid(occ[stream], a.nvec, sm_count), st, a);
+    return launch_pdl(kern[stream], phase_grid(occupancy(kern[stream]), a.nvec, sm_count), st, a);
 }
 
 cudaError_t launch_phase_bwd_start(const PhaseArgs &a, bool stream, cudaStream_t st, int sm_count) {
-    static const int occ[2] = {occupancy(k_phase_bwd_start<false>), occupancy(k_phase_bwd_start<true>)};
     void (*kern[2])(PhaseArgs) = {k_phase_bwd_start<false>, k_phase_bwd_start<true>};
-    return launch_pdl(kern[stream], phase_grid(occ[stream], a.nvec, sm_count), st, a);
+    return launch_pdl(kern[stream], phase_grid(occupancy(kern[stream]), a.nvec, sm_count), st, a);
 }
 
 }  // namespace grv
