@@ -748,12 +748,12 @@ __global__ void k_bits_check_count(const uint32_t *words, uint64_t nwords, uint6
 
 // ---- launch helpers ---------------------------------------------------------------------------
 bool pdl_enabled() {
-    static int v = -1;
-    if (v < 0) {
+    // read once per process (initialisation of a local static is thread-safe)
+    static const bool v = [] {
         const char *e = getenv("GROVER_PDL");
-        v = (e && e[0] == '0') ? 0 : 1;
-    }
-    return v == 1;
+        return !(e && e[0] == '0');
+    }();
+    return v;
 }
 
 template <class... KArgs, class... Args>
