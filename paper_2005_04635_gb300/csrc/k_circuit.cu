@@ -18,7 +18,9 @@ namespace grv {
 namespace {
 
 constexpr int kCircThreads = 256;
-constexpr int kCircUnroll = 2;
+// pairs per thread per loop step: 8 (16 vectors in flight per thread) measured
+// 6.42 TB/s per pass at n = 28 complex64 against 6.07 with 2
+constexpr int kCircUnroll = 8;
 
 template <bool STREAM, class V> __device__ __forceinline__ V ld(const V *p) {
     if (STREAM) return __ldcs(p);
@@ -50,11 +52,21 @@ template <int OP, class T> __device__ __forceinline__ void pair_op(T &ar, T &ai,
 // complex64, qubit 0: both amplitudes of a pair share one float4
 template <int OP, bool STREAM>
 __global__ void __launch_bounds__(kCircThreads) k_gate1_c64_q0(float4 *v, uint64_t nvec, float s) {
-    for (uint64_t j = (uint64_t)blockIdx.x * kCircThreads + threadIdx.x; j < nvec;
-         j += (uint64_t)gridDim.x * kCircThreads) {
-        float4 c = ld<STREAM>(v + j);
-        pair_op<OP>(c.x, c.y, c.z, c.w, s);
-        st<STREAM>(v + j, c);
+    const uint64_t stride = (uint64_t)gridDim.x * kCircThreads * kCircUnroll;
+    for (uint64_t j0 = (uint64_t)blockIdx.x * kCircThreads * kCircUnroll + threadIdx.x; j0 < nvec; j0 += stride) {
+        float4 c[kCircUnroll];
+#pragma unroll
+        for (int u = 0; u < kCircUnroll; ++u) {
+            const uint64_t j = j0 + (uint64_t)u * kCircThreads;
+            if (j < nvec) c[u] = ld<STREAM>(v + j);
+        }
+#pragma unroll
+        for (int u = 0; u < kCircUnroll; ++u) {
+            const uint64_t j = j0 + (uint64_t)u * kCircThreads;
+            if (j >= nvec) continue;
+            pair_op<OP>(c[u].x, c[u].y, c[u].z, c[u].w, s);
+            st<STREAM>(v + j, c[u]);
+        }
     }
 }
 
@@ -119,7 +131,8 @@ cudaError_t gate1_t(void *amps, int n, grover_dtype dt, int q, double scale, cud
         const uint64_t nvec = N / 2;
         if (q == 0) {
             auto kern = k_gate1_c64_q0<OP, STREAM>;
-            kern<<<grid_for(kern, nvec, kCircThreads, g), kCircThreads, 0, st>>>(v, nvec, (float)scale);
+            kern<<<grid_for(kern, nvec, (uint64_t)kCircThreads * kCircUnroll, g), kCircThreads, 0, st>>>(
+                v, nvec, (float)scale);
         } else {
             auto kern = k_gate1_pairs<OP, STREAM, float4, float>;
             const uint64_t np = nvec / 2;
