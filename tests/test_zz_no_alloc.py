@@ -7,10 +7,12 @@ oracle gives from the same stored start, within the tolerances of the other
 parity tests.  This file is collected last on purpose; it passes alone in a
 fresh process and after the other tests.
 
-Oracle bound: an iteration adds an error vector of norm <= 3u (one rounding
-per stored amplitude, norm <= u; the rounding of 2 mu shared by all N
-amplitudes, norm <= sqrt(N) u 2|mu| <= 2u) and is unitary, so after k
-iterations ||gpu - oracle||_2 <= 3 k u (u = 2^-24 complex64, 2^-53 complex128).
+Oracle bounds: complex64, the worst-case bound of c64_bounds (FP32 tile sums
+of the mean and two roundings per stored amplitude); complex128 (exact sums),
+an iteration adds an error vector of norm <= 3u (one rounding per stored
+amplitude, norm <= u; the rounding of 2 mu shared by all N amplitudes, norm
+<= sqrt(N) u 2|mu| <= 2u, u = 2^-53) and is unitary, so after k iterations
+||gpu - oracle||_2 <= 3 k u.
 """
 from __future__ import annotations
 
