@@ -255,10 +255,12 @@ k_topm(const T *amps, uint64_t nvec, Cand *cand, unsigned *ticket, Cand *final_o
     // A thread visits indices in increasing order, so an amplitude equal to one
     // that already failed to enter can never enter later (its probability ties
     // and its index is larger): equal magnitudes are skipped by comparing bits.
+    // Four vectors per thread are loaded before any is examined (more 16-byte
+    // loads in flight for the HBM stream), then examined in increasing order.
+    constexpr int KU = 4;
     float b32 = -1.0f;
     uint64_t seen_hi = ~0ull, seen_lo = ~0ull;
-    for (uint64_t i = (uint64_t)blockIdx.x * kThreads + threadIdx.x; i < nvec; i += (uint64_t)gridDim.x * kThreads) {
-        const V c = __ldcs(v + i);
+    auto visit = [&](const V c, uint64_t i) {
         if constexpr (APV == 2) {
             const float e0 = fmaf(c.x, c.x, c.y * c.y);
             const float e1 = fmaf(c.z, c.z, c.w * c.w);
@@ -286,6 +288,16 @@ k_topm(const T *amps, uint64_t nvec, Cand *cand, unsigned *ticket, Cand *final_o
                 }
             }
         }
+    };
+    const uint64_t S = (uint64_t)gridDim.x * kThreads;
+    for (uint64_t i0 = (uint64_t)blockIdx.x * kThreads + threadIdx.x; i0 < nvec; i0 += KU * S) {
+        V cc[KU];
+#pragma unroll
+        for (int u = 0; u < KU; ++u)
+            if (i0 + u * S < nvec) cc[u] = __ldcs(v + i0 + u * S);
+#pragma unroll
+        for (int u = 0; u < KU; ++u)
+            if (i0 + u * S < nvec) visit(cc[u], i0 + u * S);
     }
     block_merge<K>(t, cand + (size_t)blockIdx.x * K);
 
