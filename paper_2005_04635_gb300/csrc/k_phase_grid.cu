@@ -232,6 +232,12 @@ __device__ RepSums replica_sums(const float2 *rep, uint32_t m, bool want_p) {
 }
 
 // ---- forward sweep -----------------------------------------------------------
+// U vectors per thread per summation group: slices of at least kPgWideVecs
+// vectors take U = 8, one FP32 pairwise sum of 16 amplitudes per exact add
+// (half the adds), smaller ones U = 4, whose threads hold too few vectors.
+constexpr uint32_t kPgWideVecs = 6 * kPgThreads;
+
+template <int U>
 __global__ void __launch_bounds__(kPgThreads, 1) k_phase_grid_fwd(PhaseGridArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float4 s_kap, s_can;
@@ -263,10 +269,10 @@ __global__ void __launch_bounds__(kPgThreads, 1) k_phase_grid_fwd(PhaseGridArgs 
         }
         u128 v[2] = {0, 0};
         double sd[2] = {0.0, 0.0};
-        for (uint32_t j0 = threadIdx.x; j0 < nv; j0 += kU * kPgThreads) {
-            float gr[2 * kU], gi[2 * kU];
+        for (uint32_t j0 = threadIdx.x; j0 < nv; j0 += U * kPgThreads) {
+            float gr[2 * U], gi[2 * U];
 #pragma unroll
-            for (int u = 0; u < kU; ++u) {
+            for (int u = 0; u < U; ++u) {
                 const uint32_t j = j0 + u * kPgThreads;
                 if (j >= nv) {
                     gr[2 * u] = gr[2 * u + 1] = gi[2 * u] = gi[2 * u + 1] = 0.f;
@@ -287,8 +293,8 @@ __global__ void __launch_bounds__(kPgThreads, 1) k_phase_grid_fwd(PhaseGridArgs 
                 gr[2 * u + 1] = c1.x;
                 gi[2 * u + 1] = c1.y;
             }
-            fix_add<4>(v[0], sd[0], pairwise<2 * kU>(gr));
-            fix_add<4>(v[1], sd[1], pairwise<2 * kU>(gi));
+            fix_add<4>(v[0], sd[0], pairwise<2 * U>(gr));
+            fix_add<4>(v[1], sd[1], pairwise<2 * U>(gi));
         }
         const long long nxt = t + 1;
         const bool last = nxt >= a.K;
@@ -591,7 +597,8 @@ cudaError_t launch_phase_table(const double *phi, const double *vphi, long long 
 
 cudaError_t launch_phase_grid(const PhaseGridArgs &a, bool backward, unsigned G, size_t smem, cudaStream_t st) {
     if (backward) return launch_coop(k_phase_grid_bwd, G, smem, st, a);
-    return launch_coop(k_phase_grid_fwd, G, smem, st, a);
+    if (a.slice_vecs >= kPgWideVecs) return launch_coop(k_phase_grid_fwd<8>, G, smem, st, a);
+    return launch_coop(k_phase_grid_fwd<4>, G, smem, st, a);
 }
 
 }  // namespace grv

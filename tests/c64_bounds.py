@@ -32,12 +32,13 @@ The generalised phase iterator D(vphi) O(phi) (one pass on a stored state c):
     c_x, a complex product within sqrt(5) u |c_x| of exact (Brent, Percival
     and Zimmermann's bound; 2u with fused multiply-adds): (1 + sqrt(5)) u
     |c_x| + O(u^2) in all;
-  * kappa = (1 - e^{i vphi}) <O c> comes from 8-amplitude FP32 tile sums added
-    exactly (the marked correction in FP64), and |1 - e^{i vphi}| <= 2, so
-    kappa's error, met by all N amplitudes, is an error vector of norm
-    <= 2 gamma_3 ||c||; its float pair adds 2^-45 ||c||;
+  * kappa = (1 - e^{i vphi}) <O c> comes from FP32 tile sums of 8 amplitudes
+    (16 in the on-chip forward sweep's wide slices) added exactly (the marked
+    correction in FP64), and |1 - e^{i vphi}| <= 2, so kappa's error, met by
+    all N amplitudes, is an error vector of norm <= 2 gamma_4 ||c||; its float
+    pair adds 2^-45 ||c||;
   * c - kappa_hi - kappa_lo rounds twice: 2u ||c'||.
-  rho_phase <= (1 + sqrt(5) + 6 + 2) u + O(u^2) <= 12u + 64u^2.  The backward
+  rho_phase <= (1 + sqrt(5) + 8 + 2) u + O(u^2) <= 14u + 64u^2.  The backward
   sweep applies the same operations (subtraction, then rotation) to the state
   and to the adjoint, each within the same rho per pass.
 
@@ -52,7 +53,7 @@ import math
 
 U = 2.0 ** -24
 RHO = {"default": 10 * U + 64 * U * U, "tile8": 8 * U + 64 * U * U, "exact": 2 * U + 32 * U * U,
-       "phase": 12 * U + 64 * U * U}
+       "phase": 14 * U + 64 * U * U}
 
 
 def rho_fp64(n):

@@ -16,7 +16,7 @@ checked through the C ABI:
   below Zalka's bound sin^2((2K+1) theta).
 
 Tolerances (c64_bounds).  States: every pass adds an error vector of norm at
-most rho ||psi||, rho = 12u + 64u^2 (the phase product, kappa from FP32 tile
+most rho ||psi||, rho = 14u + 64u^2 (the phase product, kappa from FP32 tile
 sums, two roundings of the subtraction; u = 2^-24), and the iterator is
 unitary, so after K passes the error vector's 2-norm is within
 E = ((1 + rho)^K (1 + e0) - 1) ||psi|| (e0 = u for a rounded uniform start, 0
